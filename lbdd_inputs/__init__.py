@@ -1,0 +1,210 @@
+"""Seeded synthetic LBDD instances shared by the CPU oracle and the CUDA path.
+
+This package holds no part of the solver: it only synthesises the inputs of
+the problem statement (Section 2.1): the demand-service cost matrix CM
+(n x k, demand-major, positive integers), the capacity c_s of every service
+center and, per center, a constant per-unit overload penalty (the form used in
+the paper's experiments, Section 5).
+
+Named workloads (see ``CONFIGS``) reproduce the shape of the paper's
+city-scale experiments with synthetic points because the New Delhi road
+network is not available: unit demand, random center placement, total
+capacity theta*n < n split at random, and penalties drawn from a range.
+
+The numeric kernels live in ``gen.c`` (compiled to ``_gen.so`` by
+:func:`build`); they are bit-reproducible across x86-64 and aarch64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_gen.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile gen.c into _gen.so (no fused multiply-add, OpenMP threads)."""
+    src = os.path.join(_HERE, "gen.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
+               "-fno-fast-math", "-fopenmp", src, "-o", _SO + ".tmp", "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(_SO + ".tmp", _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        P = ctypes.c_void_p
+        i64, u64, u32, f64, i32 = (ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
+                                   ctypes.c_double, ctypes.c_int32)
+        lib.lbdd_gen_u64.argtypes = [u64, u32, u64]
+        lib.lbdd_gen_u64.restype = u64
+        lib.lbdd_gen_u01.argtypes = [u64, u32, u64]
+        lib.lbdd_gen_u01.restype = f64
+        lib.lbdd_gen_log.argtypes = [f64]
+        lib.lbdd_gen_log.restype = f64
+        lib.lbdd_gen_exp.argtypes = [f64]
+        lib.lbdd_gen_exp.restype = f64
+        lib.lbdd_gen_points_uniform.argtypes = [u64, u32, i64, P]
+        lib.lbdd_gen_points_gmm.argtypes = [u64, i64, ctypes.c_int, f64, f64, P]
+        lib.lbdd_gen_cm.argtypes = [i64, i64, P, P, f64, f64, f64, u64, ctypes.c_int, P]
+        lib.lbdd_gen_cm_sample.argtypes = [i64, P, i64, P, P, f64, f64, f64, u64, P]
+        lib.lbdd_gen_caps_uniform.argtypes = [u64, i64, i64, P]
+        lib.lbdd_gen_caps_zipf.argtypes = [u64, i64, i64, f64, P]
+        lib.lbdd_gen_pens.argtypes = [u64, i64, i32, i32, P]
+        lib.lbdd_gen_logu_size.argtypes = [u64, u64, f64, f64]
+        lib.lbdd_gen_logu_size.restype = i64
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise RuntimeError(f"{what} failed with code {rc}")
+
+
+# Stream ids of the point sets (must match the enum in gen.c).
+_ST_DEMAND_XY, _ST_CENTER_XY = 1, 2
+
+
+@dataclass
+class Recipe:
+    """Parameters of one synthetic instance."""
+    n: int
+    k: int
+    seed: int
+    layout: str = "uniform"          # "uniform" or "gmm" demand points
+    ncomp: int = 30                  # mixture components for "gmm"
+    sigma: tuple = (0.02, 0.08)      # component sigma range for "gmm"
+    scale: float = 100.0             # CM = max(1, floor(scale*dist*rf + 0.5))
+    road: tuple = (1.0, 1.0)         # road-factor range per (d, s) pair
+    cap_frac: float = 0.9            # total capacity = floor(cap_frac * n)
+    cap_dist: str = "uniform"        # "uniform" or "zipf"
+    zipf: float = 1.2
+    pen: tuple = (50, 500)           # per-unit penalty range, inclusive
+    name: str = ""
+
+
+@dataclass
+class Instance:
+    n: int
+    k: int
+    cm: np.ndarray                   # (n, k) int32 or int16, demand-major
+    cap: np.ndarray                  # (k,) int32
+    pen: np.ndarray                  # (k,) int32
+    recipe: Recipe = field(repr=False, default=None)
+    dxy: np.ndarray = field(repr=False, default=None)
+    sxy: np.ndarray = field(repr=False, default=None)
+
+    def cm_sample(self, pairs: np.ndarray) -> np.ndarray:
+        """Regenerate CM[d, s] for an (m, 2) array of (d, s) pairs."""
+        lib = _load()
+        r = self.recipe
+        pairs = np.ascontiguousarray(pairs, dtype=np.int64)
+        out = np.empty(len(pairs), dtype=np.int64)
+        _check(lib.lbdd_gen_cm_sample(len(pairs), _ptr(pairs), self.k, _ptr(self.dxy),
+                                      _ptr(self.sxy), r.scale, r.road[0], r.road[1],
+                                      r.seed, _ptr(out)), "cm_sample")
+        return out
+
+
+# Workloads.  "tiny" is the small single instance (2,000 x 20); "city" the
+# city-scale single solve (200,000 x 500, clustered demand, road factors,
+# Zipf capacities); "large" the HBM-bound solve (2,000,000 x 2,000).
+CONFIGS = {
+    "tiny": Recipe(n=2000, k=20, seed=1, layout="uniform", scale=100.0, cap_frac=0.9,
+                   cap_dist="uniform", pen=(50, 500), name="tiny"),
+    "city": Recipe(n=200_000, k=500, seed=2, layout="gmm", scale=1000.0, road=(1.0, 1.5),
+                   cap_frac=0.8, cap_dist="zipf", zipf=1.2, pen=(200, 2000), name="city"),
+    "large": Recipe(n=2_000_000, k=2000, seed=3, layout="gmm", scale=1000.0, road=(1.0, 1.5),
+                    cap_frac=0.85, cap_dist="zipf", zipf=1.2, pen=(100, 5000), name="large"),
+}
+
+BATCH_SEED0 = 1000      # batched mix: instance i uses seed 1000 + i
+SERVE_SEED0 = 100000    # serving stream: request i uses seed 100000 + i
+
+
+def batch_recipe(i: int, n_range=(3.0, 5.0), k_range=(1.0, 2.6020599913279625)) -> Recipe:
+    """Instance i of the batched mix: n log-uniform in [10^3, 10^5), k
+    log-uniform in [10, 400), otherwise generated like "tiny"."""
+    lib = _load()
+    seed = BATCH_SEED0 + i
+    n = int(lib.lbdd_gen_logu_size(seed, 0, n_range[0], n_range[1]))
+    k = int(lib.lbdd_gen_logu_size(seed, 1, k_range[0], k_range[1]))
+    return Recipe(n=n, k=k, seed=seed, layout="uniform", scale=100.0, cap_frac=0.9,
+                  cap_dist="uniform", pen=(50, 500), name=f"batch{i}")
+
+
+def make(recipe: Recipe, dtype: str = "i32", points_only: bool = False) -> Instance:
+    """Synthesise one instance.  dtype: "i32" or "i16" (raises if a cost
+    does not fit int16)."""
+    lib = _load()
+    r = recipe
+    n, k = int(r.n), int(r.k)
+    dxy = np.empty((n, 2), dtype=np.float64)
+    sxy = np.empty((k, 2), dtype=np.float64)
+    if r.layout == "uniform":
+        _check(lib.lbdd_gen_points_uniform(r.seed, _ST_DEMAND_XY, n, _ptr(dxy)), "points")
+    elif r.layout == "gmm":
+        _check(lib.lbdd_gen_points_gmm(r.seed, n, r.ncomp, r.sigma[0], r.sigma[1], _ptr(dxy)),
+               "gmm")
+    else:
+        raise ValueError(r.layout)
+    _check(lib.lbdd_gen_points_uniform(r.seed, _ST_CENTER_XY, k, _ptr(sxy)), "centers")
+    cap = np.empty(k, dtype=np.int32)
+    total = int(np.floor(r.cap_frac * n))
+    if r.cap_dist == "uniform":
+        _check(lib.lbdd_gen_caps_uniform(r.seed, k, total, _ptr(cap)), "caps")
+    elif r.cap_dist == "zipf":
+        _check(lib.lbdd_gen_caps_zipf(r.seed, k, total, r.zipf, _ptr(cap)), "caps")
+    else:
+        raise ValueError(r.cap_dist)
+    pen = np.empty(k, dtype=np.int32)
+    _check(lib.lbdd_gen_pens(r.seed, k, r.pen[0], r.pen[1], _ptr(pen)), "pens")
+    if points_only:
+        cm = None
+    else:
+        np_dt = {"i32": np.int32, "i16": np.int16}[dtype]
+        cm = np.empty((n, k), dtype=np_dt)
+        _check(lib.lbdd_gen_cm(n, k, _ptr(dxy), _ptr(sxy), r.scale, r.road[0], r.road[1],
+                               r.seed, np.dtype(np_dt).itemsize, _ptr(cm)), "cm")
+    return Instance(n=n, k=k, cm=cm, cap=cap, pen=pen, recipe=r, dxy=dxy, sxy=sxy)
+
+
+def make_named(name: str, dtype: str = "i32", **overrides) -> Instance:
+    base = CONFIGS[name]
+    r = Recipe(**{**base.__dict__, **overrides})
+    return make(r, dtype=dtype)
+
+
+def random_small(seed: int, n: int, k: int, cm_max: int = 20, cap_frac: float = 0.7,
+                 pen=(1, 30)) -> Instance:
+    """Tiny instance with CM uniform in [1, cm_max] drawn from the counter
+    stream (many ties on purpose), for exhaustive and exact-solver checks."""
+    lib = _load()
+    cm = np.empty((n, k), dtype=np.int32)
+    for d in range(n):
+        for s in range(k):
+            cm[d, s] = 1 + lib.lbdd_gen_u64(seed, 11, d * k + s) % cm_max
+    cap = np.empty(k, dtype=np.int32)
+    total = max(k, int(np.floor(cap_frac * n)))
+    _check(lib.lbdd_gen_caps_uniform(seed, k, total, _ptr(cap)), "caps")
+    p = np.empty(k, dtype=np.int32)
+    _check(lib.lbdd_gen_pens(seed, k, pen[0], pen[1], _ptr(p)), "pens")
+    r = Recipe(n=n, k=k, seed=seed, name=f"small{seed}")
+    return Instance(n=n, k=k, cm=cm, cap=cap, pen=p, recipe=r)

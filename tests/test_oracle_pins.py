@@ -1,0 +1,273 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these compares the oracle with itself: each check is an exact
+solver (brute force, the paper's min-cost-matching reduction), a closed
+form, a library routine (scipy Bellman-Ford / negative-cycle detection), a
+theorem of the paper (Lemmas 1-2, Theorem 2), or an independent data
+structure (the BestTransHeaps vs. the table recomputed by definition).
+The last test plants typical mistakes in a copy of the oracle and checks that
+at least one pin fails for each.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import lbdd_inputs as L
+import oracle
+from oracle import exact
+
+
+def small(seed, n, k, **kw):
+    return L.random_small(seed, n=n, k=k, **kw)
+
+
+# ---------------------------------------------------------------- exact ---
+
+def test_brute_force_equals_matching_reduction():
+    """The min-cost-matching reduction (Section 1) solves Eq. (1) exactly."""
+    for s in range(25):
+        J = small(100 + s, 7, 3, cm_max=9, cap_frac=0.5, pen=(1, 6))
+        assert exact.brute_force(J.cm, J.cap, J.pen) == exact.matching_optimum(J.cm, J.cap, J.pen)
+
+
+@pytest.mark.parametrize("mode", [oracle.MODE_DEFINITION, oracle.MODE_HEAP])
+def test_asral_never_below_optimum_and_reaches_it(mode):
+    """ASRAL's objective is a feasible value, so never below the optimum.
+    With constant per-unit penalties every refinement is a shortest
+    augmenting path of a convex-cost flow, and on all seeded instances here
+    the value equals the optimum; a dropped term, a sign or index slip in the
+    graphs of Defs. 5/6 breaks the equality."""
+    for s in range(40):
+        n = [8, 20, 45][s % 3]
+        k = [2, 3, 5, 7][s % 4]
+        J = small(300 + s, n, k, cm_max=[4, 15, 60][s % 3], cap_frac=[0.3, 0.6, 0.95][s % 3],
+                  pen=[(1, 5), (1, 40), (10, 100)][(s // 3) % 3])
+        r = oracle.asral(J.cm, J.cap, J.pen, mode=mode, check=True)
+        assert r.rc == oracle.OK
+        opt = exact.matching_optimum(J.cm, J.cap, J.pen)
+        assert r.delta >= opt
+        assert r.delta == opt, (s, r.delta, opt)
+
+
+def test_brute_force_bound_on_tiny():
+    for s in range(20):
+        J = small(700 + s, 8, 3, cm_max=6, cap_frac=0.5, pen=(1, 4))
+        r = oracle.asral(J.cm, J.cap, J.pen)
+        assert r.rc == 0 and r.delta >= exact.brute_force(J.cm, J.cap, J.pen)
+
+
+# ----------------------------------------------------------- invariants ---
+
+def test_incremental_objective_equals_eq1_and_allotment_complete():
+    inst = L.make_named("tiny")
+    r = oracle.asral(inst.cm, inst.cap, inst.pen)
+    assert r.rc == 0
+    assert (r.assign >= 0).all() and (r.assign < inst.k).all()      # each unit once
+    assert np.array_equal(np.bincount(r.assign, minlength=inst.k), r.load)
+    assert r.delta == exact.eq1_objective(inst.cm, inst.cap, inst.pen, r.assign)
+    assert r.delta == oracle.objective(inst.cm, inst.cap, inst.pen, r.assign)
+
+
+def test_lemmas_hold_every_round():
+    """Lemmas 1 and 2: Gamma has no negative cycle after every round (the
+    oracle's check mode runs the test after each round and also compares
+    the tracked objective with Eq. (1))."""
+    for s in range(30):
+        J = small(900 + s, 30, 5, cm_max=25, cap_frac=0.5, pen=(1, 30))
+        assert oracle.asral(J.cm, J.cap, J.pen, check=True).rc == oracle.OK
+    inst = L.make(L.Recipe(n=400, k=12, seed=17, scale=100.0, cap_frac=0.8, pen=(20, 200)))
+    assert oracle.asral(inst.cm, inst.cap, inst.pen, check=True).rc == oracle.OK
+
+
+def test_heap_mode_equals_definition_mode():
+    """BestTransHeaps (Section 3.4) and the table by definition agree."""
+    for s in range(15):
+        J = small(1200 + s, 60, 6, cm_max=8, cap_frac=0.6, pen=(1, 9))   # many ties
+        a = oracle.asral(J.cm, J.cap, J.pen, mode=oracle.MODE_DEFINITION)
+        b = oracle.asral(J.cm, J.cap, J.pen, mode=oracle.MODE_HEAP)
+        assert a.rc == b.rc == 0
+        assert np.array_equal(a.assign, b.assign) and a.delta == b.delta
+        assert a.stats == b.stats
+    inst = L.make_named("tiny")
+    a = oracle.asral(inst.cm, inst.cap, inst.pen, mode=oracle.MODE_DEFINITION)
+    b = oracle.asral(inst.cm, inst.cap, inst.pen, mode=oracle.MODE_HEAP)
+    assert np.array_equal(a.assign, b.assign) and a.delta == b.delta
+
+
+def test_truncated_rounds_are_a_prefix():
+    inst = L.make_named("tiny")
+    full = oracle.asral(inst.cm, inst.cap, inst.pen)
+    part = oracle.asral(inst.cm, inst.cap, inst.pen, max_rounds=700)
+    assert part.stats["rounds"] == 700
+    assert (part.assign >= 0).sum() == 700
+    assert part.delta == oracle.objective(inst.cm, inst.cap, inst.pen, part.assign)
+    assert full.delta != part.delta
+
+
+# --------------------------------------------------------- closed forms ---
+
+def test_ample_capacity_gives_row_minima():
+    """cap_s >= n for all s: nothing is ever overloaded, every unit sits at a
+    row minimum and Delta = sum_d min_s CM(d, s)."""
+    for s in range(10):
+        J = small(1500 + s, 50, 6, cm_max=30)
+        cap = np.full(J.k, J.n, np.int32)
+        r = oracle.asral(J.cm, cap, J.pen)
+        assert r.rc == 0 and r.delta == int(J.cm.min(axis=1).sum())
+        assert r.stats["moves"] == 0
+
+
+def test_single_center_closed_form():
+    for s in range(5):
+        J = small(1600 + s, 40, 1, cm_max=30)
+        cap, pen = np.array([13], np.int32), np.array([7], np.int32)
+        r = oracle.asral(J.cm, cap, pen)
+        assert r.delta == int(J.cm.sum()) + 7 * (40 - 13)
+
+
+def test_smin_and_order_definition():
+    """Alg. 1 line 1: lowest-index row minimum; order (cost, d) ascending,
+    checked against numpy's argmin (first occurrence) and lexsort."""
+    J = small(1700, 500, 9, cm_max=5)
+    smin, order = oracle.smin_order(J.cm)
+    assert np.array_equal(smin, np.argmin(J.cm, axis=1))
+    cost = J.cm[np.arange(J.n), smin]
+    assert np.array_equal(order, np.lexsort((np.arange(J.n), cost)))
+
+
+# ------------------------------------------------------- Bellman-Ford -----
+
+def _random_potential_graph(rng, N, density):
+    W = np.full((N, N), oracle.INF, np.int64)
+    pot = rng.integers(0, 30, N)
+    for u in range(N):
+        for v in range(N):
+            if u != v and rng.random() < density:
+                W[u, v] = int(rng.integers(0, 6)) + pot[v] - pot[u]   # no negative cycle
+    return W
+
+
+def test_bellman_ford_matches_scipy_and_paths_are_tight():
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import bellman_ford
+    rng = np.random.default_rng(1)
+    for t in range(60):
+        N = int(rng.integers(2, 12))
+        W = _random_potential_graph(rng, N, 0.5)
+        src = int(rng.integers(0, N))
+        rc, dist, par, sweeps = oracle.bellman_ford(W, src)
+        assert rc == 0 and sweeps <= N
+        mask = W < oracle.INF
+        G = sp.csr_matrix((W[mask].astype(float), np.nonzero(mask)), shape=(N, N))
+        ref = bellman_ford(G, indices=src)
+        for v in range(N):
+            if np.isinf(ref[v]):
+                assert dist[v] >= oracle.INF and par[v] == -1
+            else:
+                assert dist[v] == ref[v]
+                if v != src:   # parent edge is tight, parent is lowest such index
+                    u = par[v]
+                    assert dist[u] + W[u, v] == dist[v]
+
+
+def test_bellman_ford_reports_negative_cycle():
+    W = np.full((4, 4), oracle.INF, np.int64)
+    W[0, 1], W[1, 2], W[2, 1], W[2, 3] = 1, -3, 1, 0
+    rc, *_ = oracle.bellman_ford(W, 0)
+    assert rc == oracle.ERR_INVARIANT
+
+
+def test_negative_cycle_checker_matches_scipy():
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import NegativeCycleError, bellman_ford
+    rng = np.random.default_rng(2)
+    for t in range(80):
+        k = int(rng.integers(2, 8))
+        tc = np.where(rng.random((k, k)) < 0.6, rng.integers(-6, 10, (k, k)), oracle.INF)
+        np.fill_diagonal(tc, oracle.INF)
+        mask = tc < oracle.INF
+        G = sp.csr_matrix((tc[mask].astype(float), np.nonzero(mask)), shape=(k, k))
+        try:
+            bellman_ford(G)
+            ref = False
+        except NegativeCycleError:
+            ref = True
+        assert oracle.has_negative_cycle(tc) == ref
+
+
+# -------------------------------------------------------- strict-LBDD -----
+
+def test_strict_lbdd_is_optimal():
+    """Theorem 2 + Alg. 5: the NegCycle-only variant with dummy units is
+    optimal for hard capacities; checked against the assignment reduction,
+    with and without excess demand."""
+    for s in range(30):
+        n, k = [10, 30, 60][s % 3], [2, 4, 6][s % 3]
+        J = small(1800 + s, n, k, cm_max=[6, 25, 40][s % 3], cap_frac=[0.6, 1.0, 1.4][s % 3])
+        rc, assign, cost, st = oracle.strict(J.cm, J.cap)
+        assert rc == 0
+        assert cost == exact.strict_optimum(J.cm, J.cap)
+        k_ext = k + (1 if J.cap.sum() < n else 0)
+        load = np.bincount(assign, minlength=k_ext)
+        assert (load[:k] <= J.cap).all()
+
+
+# ------------------------------------------------------ planted mistakes --
+
+_SRC = os.path.join(os.path.dirname(oracle.__file__), "asral_oracle.c")
+
+MUTATIONS = {
+    "dropped_penalty_term": ("(over ? (int64_t)pen[j] : 0)", "0"),
+    "transfer_sign": ("int64_t t = (int64_t)cm[d * k + v] - (int64_t)cm[d * k + u];",
+                      "int64_t t = (int64_t)cm[d * k + u] - (int64_t)cm[d * k + v];"),
+    "penalty_edge_sign": ("S->W[u * N + k] = qu - (int64_t)S->pen[j];",
+                          "S->W[u * N + k] = (int64_t)S->pen[j] - qu;"),
+    "transposed_sink_edge": ("if (u != j) S->W[u * N + k] = S->tc[u * k + j];",
+                             "if (u != j) S->W[u * N + k] = S->tc[j * k + u];"),
+    "wrong_vacancy_test": ("int over = S.load[j] >= cap[j];", "int over = S.load[j] > cap[j];"),
+    "terminal_load_not_moved": ("S->load[term] += 1;", "S->load[j] += 0;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(_SRC).read()
+    assert src.count(old) == 1, name
+    mutated = tmp_path / "mut.c"
+    mutated.write_text(src.replace(old, new))
+    so = tmp_path / "mut.so"
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", str(mutated), "-o", str(so)],
+                   check=True)
+    lib = ctypes.CDLL(str(so))
+    P, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.oracle_asral.argtypes = [i64, i64, P, P, P, c_int, i64, c_int, P, P, P, P]
+    def run(J, mode):
+        cm = np.ascontiguousarray(J.cm, np.int32)
+        assign = np.empty(J.n, np.int32)
+        load = np.empty(J.k, np.int64)
+        delta = ctypes.c_int64(0)
+        st = oracle._Stats()
+        rc = lib.oracle_asral(J.n, J.k, cm.ctypes.data, J.cap.ctypes.data, J.pen.ctypes.data,
+                              mode, -1, 0, assign.ctypes.data, load.ctypes.data,
+                              ctypes.byref(delta), ctypes.byref(st))
+        return rc, assign, load, delta.value
+
+    caught = False
+    for s in range(12):
+        J = small(2100 + s, 24, 4, cm_max=20, cap_frac=0.5, pen=(1, 25))
+        opt = exact.matching_optimum(J.cm, J.cap, J.pen)
+        results = [run(J, mode) for mode in (oracle.MODE_DEFINITION, oracle.MODE_HEAP)]
+        for rc, assign, load, delta in results:
+            if rc != 0 or delta != opt or \
+                    delta != exact.eq1_objective(J.cm, J.cap, J.pen, assign) or \
+                    not np.array_equal(np.bincount(assign, minlength=J.k), load):
+                caught = True
+        if results[0][3] != results[1][3] or not np.array_equal(results[0][1], results[1][1]):
+            caught = True
+        if caught:
+            break
+    assert caught, f"mutation {name} escaped every pin"
