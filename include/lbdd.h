@@ -1,0 +1,188 @@
+/*
+ * lbdd.h -- C ABI of the GB300 (sm_103a) ASRAL solver for Load Balanced
+ * Demand Distribution (LBDD).
+ *
+ * Problem (paper Section 2.1, "Problem Statement"): given service centers
+ * S = {s_0..s_{k-1}}, demand units D = {d_0..d_{n-1}}, a cost matrix CM
+ * (n x k, positive integers, Table 1 and the cost-matrix definition of
+ * Section 2), a positive integer capacity c_s per center and a penalty q_s
+ * per center (Def. 3; here the constant per-unit form of the paper's
+ * experiments, Section 5: every unit beyond c_s costs pen[s]), find a
+ * complete allotment minimising Eq. (1):
+ *     sum_d CM(d, a(d)) + sum_s pen[s] * max(0, load_s - c_s).
+ * The solver runs ASRAL (Alg. 1 with Alg. 2 and Alg. 3) with canonical
+ * tie-breaking, so its output is one deterministic allotment that equals the
+ * project's CPU oracle bit for bit.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an lbdd_status code (0 = success); none aborts.
+ *  - CM is demand-major: entry (d, s) at index d*k + s.  Pointers flagged
+ *    "_is_device" are CUDA device pointers, otherwise host pointers.
+ *  - The library copies all inputs into device memory it owns; the caller's
+ *    buffers may be freed as soon as lbdd_create returns.
+ *  - All work is ordered on the CUDA stream given to lbdd_create (NULL = the
+ *    legacy default stream) and every call that produces a result
+ *    synchronises that stream before returning.
+ *  - An lbdd_solver is not thread-safe; distinct solvers are independent.
+ *  - A CUDA failure returns LBDD_ERR_CUDA; lbdd_last_cuda_error() gives the
+ *    CUDA error string of the most recent such failure in this process.
+ */
+#ifndef LBDD_H
+#define LBDD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lbdd_status {
+  LBDD_OK = 0,
+  LBDD_ERR_ARG = -1,        /* invalid argument (sizes, CM < 1, cap < 1, pen < 1) */
+  LBDD_ERR_OOM = -2,        /* device or host allocation failed */
+  LBDD_ERR_CUDA = -3,       /* a CUDA runtime call failed */
+  LBDD_ERR_TIMEOUT = -4,    /* a bounded wait gave up (server polling) */
+  LBDD_ERR_INVARIANT = -5,  /* Lemma 1/2 violated: Bellman-Ford did not converge */
+  LBDD_ERR_STATE = -6,      /* call not valid in the object's current state */
+  LBDD_ERR_NODEV = -7,      /* no CUDA device of compute capability 10.3 */
+  LBDD_ERR_BUDGET = -8      /* server: request larger than the memory budget */
+} lbdd_status;
+
+typedef enum lbdd_cm_dtype {
+  LBDD_CM_I32 = 0,          /* int32 entries */
+  LBDD_CM_I16 = 1           /* int16 entries (exact when every cost < 32768) */
+} lbdd_cm_dtype;
+
+typedef struct lbdd_solver lbdd_solver;   /* opaque, owned by the library */
+
+typedef struct lbdd_stats {
+  int64_t rounds;           /* rounds of Alg. 1 completed */
+  int64_t cycles_applied;   /* negative cycles removed (Alg. 2) */
+  int64_t paths_applied;    /* negative paths removed (Alg. 3) */
+  int64_t bf_calls;         /* Bellman-Ford runs to convergence */
+  int64_t bf_sweeps;        /* synchronous sweeps over all those runs */
+  int64_t bf_max_sweeps;    /* longest run, in sweeps */
+  int64_t moves;            /* demand units transferred between centers */
+  int64_t ncyc_skipped;     /* Alg. 2 calls answered without Bellman-Ford because
+                               the new unit lowered no best-transfer cost */
+  int64_t rows_scanned;     /* CM rows read by best-transfer segment rescans */
+  int64_t cm_elem_bytes;    /* 2 or 4: element size of the stored CM */
+  int64_t cluster_size;     /* CTAs per thread-block cluster used by solves */
+} lbdd_stats;
+
+/* Options for lbdd_set_option. */
+typedef enum lbdd_option {
+  LBDD_OPT_CLUSTER = 1,     /* CTAs per cluster for lbdd_solve, 1..16 (0 = auto) */
+  LBDD_OPT_NCYC_SKIP = 2,   /* 1 (default): skip Alg. 2's Bellman-Ford when the new
+                               unit lowers no best-transfer cost (exact by Lemma 1);
+                               0: always run it */
+} lbdd_option;
+
+/* Create a solver for one LBDD instance (Section 2.1 inputs).
+ *   n, k        : demand units and service centers, n >= 1, k >= 1.
+ *   cm          : n*k entries, demand-major, every entry >= 1; dtype per
+ *                 cm_dtype; host memory unless cm_is_device != 0.
+ *                 int32 input whose maximum is below 32768 is stored as
+ *                 int16 (exact, half the bytes per scan).
+ *   cap, pen    : k entries each, host memory, cap[s] >= 1, pen[s] >= 1.
+ *   cuda_stream : cudaStream_t for all work of this solver, or NULL.
+ * On success *out owns device memory of about n*k*elem + 24*n + 8*k*k bytes.
+ * Errors: LBDD_ERR_ARG, LBDD_ERR_OOM, LBDD_ERR_CUDA, LBDD_ERR_NODEV; *out
+ * is set to NULL on failure. */
+int lbdd_create(lbdd_solver** out, int32_t n, int32_t k, const void* cm, int cm_dtype,
+                int cm_is_device, const int32_t* cap, const int32_t* pen, void* cuda_stream);
+
+/* Set an lbdd_option; LBDD_ERR_ARG for an unknown option or bad value. */
+int lbdd_set_option(lbdd_solver* s, int option, int64_t value);
+
+/* Run rounds of Alg. 1 (each: allot the next unit of the MinDistance order
+ * to its most suitable center, Negative Cycle Refinement at that center,
+ * and Negative Path Refinement if the center was full).  max_rounds < 0
+ * runs to completion (n rounds in total); otherwise at most max_rounds more
+ * rounds run and a later call resumes exactly where this one stopped.
+ * Synchronous on return.  Errors: LBDD_ERR_INVARIANT (Lemma 1/2 broken,
+ * the solver is then unusable), LBDD_ERR_CUDA. */
+int lbdd_solve(lbdd_solver* s, int64_t max_rounds);
+
+/* Forget all progress: the next lbdd_solve starts again from round 0 on the
+ * CM already resident on the device (the prologue of Alg. 1 is redone).
+ * Stream-ordered; no host synchronisation. */
+int lbdd_reset(lbdd_solver* s);
+
+/* Solve m solvers' instances together in one persistent launch: each
+ * thread-block cluster takes the next unsolved instance (largest n*k first).
+ * Every solver must have been created on the same device.  max_rounds as in
+ * lbdd_solve, applied to each instance.  cluster_size 1..16 (0 = auto);
+ * max_clusters 0 = as many as fit on the GPU.  Work is issued on `stream`
+ * (NULL = legacy default stream) and synchronised before returning.
+ * Returns the first failing instance's status. */
+int lbdd_solve_batch(lbdd_solver* const* solvers, int m, int64_t max_rounds,
+                     int cluster_size, int max_clusters, void* stream);
+
+/* Tracked objective Delta of Alg. 1 (equals Eq. (1) of the current
+ * allotment).  out: host pointer. */
+int lbdd_objective(const lbdd_solver* s, int64_t* out);
+
+/* Copy the allotment: n int32 center indices, -1 for units not allotted yet.
+ * out is a host pointer unless out_is_device != 0. */
+int lbdd_assignment(const lbdd_solver* s, int32_t* out, int out_is_device);
+
+/* Copy the k center loads (int32, host). */
+int lbdd_loads(const lbdd_solver* s, int32_t* out);
+
+/* Rounds completed so far (host int64). */
+int lbdd_rounds_done(const lbdd_solver* s, int64_t* out);
+
+/* Counters of the solve so far (host struct). */
+int lbdd_get_stats(const lbdd_solver* s, lbdd_stats* out);
+
+/* Copy the solver's best-transfer table (Defs. 4-6: for every ordered pair
+ * (u, v), the cheapest transfer of a unit allotted to u over to v):
+ * tc[u*k+v] = CM(d,v) - CM(d,u) of the lexicographically smallest
+ * (cost, d), INT32_MAX if u holds no unit or u == v; td[u*k+v] = that d or
+ * -1.  k*k int32 each, host memory unless out_is_device != 0. */
+int lbdd_best_transfer_table(const lbdd_solver* s, int32_t* tc, int32_t* td, int out_is_device);
+
+/* Release everything the solver owns.  NULL is accepted. */
+void lbdd_destroy(lbdd_solver* s);
+
+/* Human-readable text of a status code (static storage). */
+const char* lbdd_strerror(int code);
+
+/* Most recent CUDA error string seen by the library (static storage). */
+const char* lbdd_last_cuda_error(void);
+
+/* ---------------------------------------------------------------------
+ * Best-transfer table from scratch (the data-parallel scan replacing the
+ * paper's Gamma-DS update, Section 3.4 "Allotment subspace multi-graph
+ * implementation" and Section 3.5.2): for an allotment assign[n] (entries
+ * < 0 are skipped), compute for every ordered pair (u, v), u != v,
+ *     T[u][v] = lexmin over d with assign[d] == u of (CM(d,v) - CM(d,u), d)
+ * with the tc/td encoding of lbdd_best_transfer_table.
+ *   cm_dev     : device CM, rows of ld >= k elements, ld*elem a multiple of
+ *                16 bytes, the allocation readable for 128 elements past the
+ *                last row; cm_dtype an lbdd_cm_dtype.
+ *   assign_dev : device int32[n], values in [-1, k).
+ *   tc_dev, td_dev : device int32[k*k] outputs.
+ *   workspace  : device scratch of lbdd_best_transfer_workspace(n, k) bytes,
+ *                owned by the caller; contents on entry are ignored.
+ *   stream     : cudaStream_t or NULL.  Asynchronous: results are ready
+ *                when the stream reaches this point.
+ * Errors: LBDD_ERR_ARG (sizes, alignment, workspace too small),
+ * LBDD_ERR_CUDA (launch failure). */
+size_t lbdd_best_transfer_workspace(int32_t n, int32_t k);
+int lbdd_best_transfer(int32_t n, int32_t k, const void* cm_dev, int cm_dtype, int64_t ld,
+                       const int32_t* assign_dev, int32_t* tc_dev, int32_t* td_dev,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/* Row pitch (elements) that lbdd_create uses for a CM of k columns, and the
+ * device pointer / pitch of a solver's stored CM (for lbdd_best_transfer). */
+int64_t lbdd_cm_pitch(int32_t k, int cm_dtype);
+int lbdd_solver_cm(const lbdd_solver* s, const void** cm_dev, int* cm_dtype, int64_t* ld);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBDD_H */

@@ -1,0 +1,302 @@
+"""Python binding of the GB300 ASRAL library (liblbdd.so, C ABI in include/lbdd.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA kernels
+of ``csrc/``.  There is no CPU fallback -- if the library cannot be built or
+loaded, or no compute-capability-10.3 GPU is present, calls raise.
+
+Names follow the C ABI (``lbdd_create`` -> :func:`create`, ...).  Device
+buffers may be passed as ``torch.Tensor`` (CUDA) or raw integer pointers;
+host buffers as numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "load", "LbddError", "Solver", "create", "solve", "reset", "solve_batch", "objective",
+    "assignment", "loads", "rounds_done", "get_stats", "best_transfer_table",
+    "best_transfer", "best_transfer_workspace", "cm_pitch", "strerror", "destroy",
+]
+
+OK = 0
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_INVARIANT, ERR_STATE, ERR_NODEV, ERR_BUDGET = \
+    -1, -2, -3, -4, -5, -6, -7, -8
+CM_I32, CM_I16 = 0, 1
+OPT_CLUSTER, OPT_NCYC_SKIP = 1, 2
+TINF = 2**31 - 1
+
+_lib = None
+
+
+class LbddError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = f"{what}: {strerror(code)} ({code})"
+        if code == ERR_CUDA and _lib is not None:
+            msg += f" [{_lib.lbdd_last_cuda_error().decode()}]"
+        super().__init__(msg)
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in (
+        "rounds", "cycles_applied", "paths_applied", "bf_calls", "bf_sweeps", "bf_max_sweeps",
+        "moves", "ncyc_skipped", "rows_scanned", "cm_elem_bytes", "cluster_size")]
+
+
+def load():
+    """Build (if stale) and load liblbdd.so; raises on any failure."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        P, i32, i64, c_int, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int,
+                                  ctypes.c_size_t)
+        lib.lbdd_create.argtypes = [ctypes.POINTER(P), i32, i32, P, c_int, c_int, P, P, P]
+        lib.lbdd_set_option.argtypes = [P, c_int, i64]
+        lib.lbdd_solve.argtypes = [P, i64]
+        lib.lbdd_reset.argtypes = [P]
+        lib.lbdd_solve_batch.argtypes = [ctypes.POINTER(P), c_int, i64, c_int, c_int, P]
+        lib.lbdd_objective.argtypes = [P, ctypes.POINTER(i64)]
+        lib.lbdd_assignment.argtypes = [P, P, c_int]
+        lib.lbdd_loads.argtypes = [P, P]
+        lib.lbdd_rounds_done.argtypes = [P, ctypes.POINTER(i64)]
+        lib.lbdd_get_stats.argtypes = [P, ctypes.POINTER(_Stats)]
+        lib.lbdd_best_transfer_table.argtypes = [P, P, P, c_int]
+        lib.lbdd_destroy.argtypes = [P]
+        lib.lbdd_destroy.restype = None
+        lib.lbdd_strerror.argtypes = [c_int]
+        lib.lbdd_strerror.restype = ctypes.c_char_p
+        lib.lbdd_last_cuda_error.argtypes = []
+        lib.lbdd_last_cuda_error.restype = ctypes.c_char_p
+        lib.lbdd_best_transfer_workspace.argtypes = [i32, i32]
+        lib.lbdd_best_transfer_workspace.restype = sz
+        lib.lbdd_best_transfer.argtypes = [i32, i32, P, c_int, i64, P, P, P, P, sz, P]
+        lib.lbdd_cm_pitch.argtypes = [i32, c_int]
+        lib.lbdd_cm_pitch.restype = i64
+        lib.lbdd_solver_cm.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(c_int),
+                                       ctypes.POINTER(i64)]
+        _lib = lib
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return load().lbdd_strerror(code).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise LbddError(rc, what)
+
+
+def _dptr(x) -> int:
+    """Device pointer of a CUDA tensor or an int."""
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda or not x.is_contiguous():
+            raise ValueError("expected a contiguous CUDA tensor")
+        return x.data_ptr()
+    raise TypeError(type(x))
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+@dataclass
+class Stats:
+    rounds: int
+    cycles_applied: int
+    paths_applied: int
+    bf_calls: int
+    bf_sweeps: int
+    bf_max_sweeps: int
+    moves: int
+    ncyc_skipped: int
+    rows_scanned: int
+    cm_elem_bytes: int
+    cluster_size: int
+
+
+def create(n, k, cm, cap, pen, stream=None, cm_dtype=None):
+    """lbdd_create.  cm: numpy (n, k) int32/int16 (host) or a CUDA tensor."""
+    lib = load()
+    cap = np.ascontiguousarray(cap, dtype=np.int32)
+    pen = np.ascontiguousarray(pen, dtype=np.int32)
+    if isinstance(cm, np.ndarray):
+        cm = np.ascontiguousarray(cm)
+        dt = {np.dtype(np.int32): CM_I32, np.dtype(np.int16): CM_I16}[cm.dtype]
+        ptr, is_dev = cm.ctypes.data, 0
+    else:
+        import torch
+        dt = {torch.int32: CM_I32, torch.int16: CM_I16}[cm.dtype] if cm_dtype is None else cm_dtype
+        ptr, is_dev = _dptr(cm), 1
+    h = ctypes.c_void_p()
+    _check(lib.lbdd_create(ctypes.byref(h), int(n), int(k), ptr, dt, is_dev, cap.ctypes.data,
+                           pen.ctypes.data, _stream_handle(stream)), "lbdd_create")
+    return h
+
+
+def set_option(h, option: int, value: int):
+    _check(load().lbdd_set_option(h, option, value), "lbdd_set_option")
+
+
+def solve(h, max_rounds: int = -1):
+    _check(load().lbdd_solve(h, int(max_rounds)), "lbdd_solve")
+
+
+def reset(h):
+    _check(load().lbdd_reset(h), "lbdd_reset")
+
+
+def solve_batch(handles, max_rounds: int = -1, cluster_size: int = 0, max_clusters: int = 0,
+                stream=None):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if hasattr(h, "value") else h for h in handles])
+    _check(load().lbdd_solve_batch(arr, len(handles), int(max_rounds), cluster_size, max_clusters,
+                                   _stream_handle(stream)), "lbdd_solve_batch")
+
+
+def objective(h) -> int:
+    v = ctypes.c_int64()
+    _check(load().lbdd_objective(h, ctypes.byref(v)), "lbdd_objective")
+    return v.value
+
+
+def rounds_done(h) -> int:
+    v = ctypes.c_int64()
+    _check(load().lbdd_rounds_done(h, ctypes.byref(v)), "lbdd_rounds_done")
+    return v.value
+
+
+def assignment(h, n: int, out=None):
+    """Host numpy copy (default) or into a CUDA int32 tensor `out`."""
+    if out is None:
+        a = np.empty(n, np.int32)
+        _check(load().lbdd_assignment(h, a.ctypes.data, 0), "lbdd_assignment")
+        return a
+    _check(load().lbdd_assignment(h, _dptr(out), 1), "lbdd_assignment")
+    return out
+
+
+def loads(h, k: int):
+    a = np.empty(k, np.int32)
+    _check(load().lbdd_loads(h, a.ctypes.data), "lbdd_loads")
+    return a
+
+
+def get_stats(h) -> Stats:
+    s = _Stats()
+    _check(load().lbdd_get_stats(h, ctypes.byref(s)), "lbdd_get_stats")
+    return Stats(**{f: getattr(s, f) for f, _ in _Stats._fields_})
+
+
+def best_transfer_table(h, k: int):
+    tc = np.empty((k, k), np.int32)
+    td = np.empty((k, k), np.int32)
+    _check(load().lbdd_best_transfer_table(h, tc.ctypes.data, td.ctypes.data, 0),
+           "lbdd_best_transfer_table")
+    return tc, td
+
+
+def solver_cm(h):
+    p, dt, ld = ctypes.c_void_p(), ctypes.c_int(), ctypes.c_int64()
+    _check(load().lbdd_solver_cm(h, ctypes.byref(p), ctypes.byref(dt), ctypes.byref(ld)),
+           "lbdd_solver_cm")
+    return p.value, dt.value, ld.value
+
+
+def cm_pitch(k: int, cm_dtype: int) -> int:
+    return int(load().lbdd_cm_pitch(k, cm_dtype))
+
+
+def best_transfer_workspace(n: int, k: int) -> int:
+    return int(load().lbdd_best_transfer_workspace(n, k))
+
+
+def best_transfer(n, k, cm_dev, cm_dtype, ld, assign_dev, tc_dev, td_dev, workspace,
+                  workspace_bytes, stream=None):
+    """lbdd_best_transfer (asynchronous on `stream`)."""
+    _check(load().lbdd_best_transfer(int(n), int(k), _dptr(cm_dev), int(cm_dtype), int(ld),
+                                     _dptr(assign_dev), _dptr(tc_dev), _dptr(td_dev),
+                                     _dptr(workspace), int(workspace_bytes),
+                                     _stream_handle(stream)), "lbdd_best_transfer")
+
+
+def destroy(h):
+    if h is not None and (not hasattr(h, "value") or h.value):
+        load().lbdd_destroy(h)
+
+
+class Solver:
+    """RAII wrapper around one lbdd_solver handle."""
+
+    def __init__(self, cm, cap, pen, stream=None, cluster: int = 0, ncyc_skip: bool = True):
+        if isinstance(cm, np.ndarray):
+            n, k = cm.shape
+        else:
+            n, k = int(cm.shape[0]), int(cm.shape[1])
+        self.n, self.k = int(n), int(k)
+        self.h = create(self.n, self.k, cm, cap, pen, stream=stream)
+        if cluster:
+            set_option(self.h, OPT_CLUSTER, cluster)
+        if not ncyc_skip:
+            set_option(self.h, OPT_NCYC_SKIP, 0)
+
+    def solve(self, max_rounds: int = -1):
+        solve(self.h, max_rounds)
+        return self
+
+    def reset(self):
+        reset(self.h)
+        return self
+
+    @property
+    def objective(self) -> int:
+        return objective(self.h)
+
+    @property
+    def rounds(self) -> int:
+        return rounds_done(self.h)
+
+    def assignment(self, out=None):
+        return assignment(self.h, self.n, out)
+
+    def loads(self):
+        return loads(self.h, self.k)
+
+    def stats(self) -> Stats:
+        return get_stats(self.h)
+
+    def table(self):
+        return best_transfer_table(self.h, self.k)
+
+    def close(self):
+        if self.h is not None:
+            destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,323 @@
+// Best-transfer table from scratch: the data-parallel replacement of the
+// paper's Gamma-DS heap maintenance (Section 3.4 "Allotment subspace
+// multi-graph implementation", Section 3.5.2), which took 74% of ASRAL's time
+// in the paper's measurements (Section 5).
+//
+//   T[u][v] = lexmin over d with assign[d] == u of (CM(d,v) - CM(d,u), d)
+//
+// Pipeline (all device-side, one stream):
+//   1. stable LSD radix sort of (assign[d], d) -> units grouped by center,
+//      ascending d inside each center (grid-wide, 8-bit digits);
+//   2. segment bounds and a list of work items, each at most kChunk rows of
+//      one center;
+//   3. the scan: each CTA streams its item's CM rows with 16-byte loads,
+//      every thread keeps a running minimum for 16 bytes' worth of columns;
+//      rows arrive in increasing d, so a strict '<' already keeps the lowest
+//      d on equal cost; the partial minima of the CTA are combined in shared
+//      memory and merged into a packed (cost, d) 64-bit table with atomicMin;
+//   4. unpack to the (tc, td) int32 pair.
+// Step 3 reads every CM byte of the allotted rows exactly once and is the
+// HBM-bound kernel; everything else moves O(n + k*k) bytes.
+#include "lbdd_device.cuh"
+
+namespace lbdd {
+
+constexpr int kTile = kThreads * 8;     // radix-sort tile (elements)
+constexpr int kChunk = 2048;            // rows per scan work item
+constexpr int kScanUnroll = 4;          // rows in flight per thread
+
+struct BtWorkspace {
+  int32_t *k0, *v0, *k1, *v1;   // radix ping-pong
+  int32_t* tile_hist;           // 256 x ntiles
+  int32_t* seg_start;           // k
+  int32_t* seg_end;             // k
+  int32_t* item_off;            // k + 1
+  unsigned long long* t64;      // k x k packed (cost + 2^31) << 32 | d
+  int64_t ntiles;
+  size_t bytes;
+};
+
+static inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static BtWorkspace carve(void* base, int32_t n, int32_t k) {
+  BtWorkspace W;
+  W.ntiles = (n + kTile - 1) / kTile;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    char* p = static_cast<char*>(base) + o;
+    o = al256(o + bytes);
+    return p;
+  };
+  W.k0 = reinterpret_cast<int32_t*>(take(4ull * n));
+  W.v0 = reinterpret_cast<int32_t*>(take(4ull * n));
+  W.k1 = reinterpret_cast<int32_t*>(take(4ull * n));
+  W.v1 = reinterpret_cast<int32_t*>(take(4ull * n));
+  W.tile_hist = reinterpret_cast<int32_t*>(take(4ull * 256 * W.ntiles));
+  W.seg_start = reinterpret_cast<int32_t*>(take(4ull * k));
+  W.seg_end = reinterpret_cast<int32_t*>(take(4ull * k));
+  W.item_off = reinterpret_cast<int32_t*>(take(4ull * (k + 1)));
+  W.t64 = reinterpret_cast<unsigned long long*>(take(8ull * k * k));
+  W.bytes = o;
+  return W;
+}
+
+size_t bt_workspace_bytes(int32_t n, int32_t k) {
+  if (n < 1 || k < 1) return 0;
+  return carve(nullptr, n, k).bytes + 256;
+}
+
+// ------------------------------------------------------------ radix sort ---
+
+// keys = assign (unallotted units -> bucket k, sorted last); values = d.
+__global__ void __launch_bounds__(kThreads) bt_init_keys(const int32_t* __restrict__ assign,
+                                                         int32_t n, int32_t k, int32_t* keys,
+                                                         int32_t* vals) {
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads) {
+    int32_t a = assign[i];
+    keys[i] = (a < 0 || a >= k) ? k : a;
+    vals[i] = (int32_t)i;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) bt_hist(const int32_t* __restrict__ keys, int32_t n,
+                                                    int shift, int32_t* tile_hist,
+                                                    int64_t ntiles) {
+  __shared__ int32_t h[256];
+  for (int i = threadIdx.x; i < 256; i += kThreads) h[i] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kTile;
+  for (int i = threadIdx.x; i < kTile; i += kThreads) {
+    const int64_t g = base + i;
+    if (g < n) atomicAdd(&h[(keys[g] >> shift) & 255], 1);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += kThreads) tile_hist[(int64_t)i * ntiles + blockIdx.x] = h[i];
+}
+
+// Exclusive scan of a device array of length m, one CTA.
+__global__ void __launch_bounds__(kThreads) bt_scan(int32_t* a, int64_t m, int32_t* total_out) {
+  __shared__ int32_t part[kThreads];
+  const int64_t per = (m + kThreads - 1) / kThreads;
+  const int64_t lo = threadIdx.x * per, hi = min(m, lo + per);
+  int32_t s = 0;
+  for (int64_t i = lo; i < hi; ++i) s += a[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t run = 0;
+    for (int t = 0; t < kThreads; ++t) { int32_t c = part[t]; part[t] = run; run += c; }
+    if (total_out) *total_out = run;
+  }
+  __syncthreads();
+  int32_t run = part[threadIdx.x];
+  for (int64_t i = lo; i < hi; ++i) { int32_t c = a[i]; a[i] = run; run += c; }
+}
+
+// Stable scatter of one tile, in order, 512 elements at a time.
+__global__ void __launch_bounds__(kThreads) bt_scatter(const int32_t* __restrict__ sk,
+                                                       const int32_t* __restrict__ sv,
+                                                       int32_t* dk, int32_t* dv, int32_t n,
+                                                       int shift,
+                                                       const int32_t* __restrict__ tile_hist,
+                                                       int64_t ntiles) {
+  __shared__ int32_t s_off[256];
+  __shared__ int32_t s_wc[kWarps * 256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t lt;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+  for (int i = tid; i < 256; i += kThreads) s_off[i] = tile_hist[(int64_t)i * ntiles + blockIdx.x];
+  const int64_t base = (int64_t)blockIdx.x * kTile;
+  for (int c = 0; c < kTile; c += kThreads) {
+    const int64_t i = base + c + tid;
+    const bool valid = i < n;
+    const int32_t key = valid ? sk[i] : 0, val = valid ? sv[i] : 0;
+    const int dig = valid ? ((key >> shift) & 255) : 256;
+    const uint32_t peers = __match_any_sync(0xffffffffu, dig);
+    const int rk = __popc(peers & lt);
+    const bool leader = (__ffs(peers) - 1) == lane;
+    for (int x = tid; x < kWarps * 256; x += kThreads) s_wc[x] = 0;
+    __syncthreads();
+    if (valid && leader) s_wc[warp * 256 + dig] = __popc(peers);
+    __syncthreads();
+    if (tid < 256) {
+      int32_t run = s_off[tid];
+      for (int ww = 0; ww < kWarps; ++ww) {
+        const int32_t cnt = s_wc[ww * 256 + tid];
+        s_wc[ww * 256 + tid] = run;
+        run += cnt;
+      }
+      s_off[tid] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      const int32_t at = s_wc[warp * 256 + dig] + rk;
+      dk[at] = key;
+      dv[at] = val;
+    }
+    __syncthreads();
+  }
+}
+
+// Segment bounds of the sorted keys.
+__global__ void __launch_bounds__(kThreads) bt_bounds(const int32_t* __restrict__ keys,
+                                                      int32_t n, int32_t k, int32_t* seg_start,
+                                                      int32_t* seg_end) {
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads) {
+    const int32_t c = keys[i];
+    if (c >= k) continue;
+    if (i == 0 || keys[i - 1] != c) seg_start[c] = (int32_t)i;
+    if (i == n - 1 || keys[i + 1] != c) seg_end[c] = (int32_t)i + 1;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) bt_items(const int32_t* __restrict__ seg_start,
+                                                     const int32_t* __restrict__ seg_end,
+                                                     int32_t k, int32_t* item_cnt,
+                                                     unsigned long long* t64) {
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < k;
+       i += (int64_t)gridDim.x * kThreads) {
+    const int32_t s = seg_end[i] - seg_start[i];
+    item_cnt[i] = (s + kChunk - 1) / kChunk;
+  }
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < (int64_t)k * k;
+       i += (int64_t)gridDim.x * kThreads)
+    t64[i] = ~0ull;
+}
+
+// ------------------------------------------------------------------ scan ---
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2)
+bt_scan_rows(const T* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
+             const int32_t* __restrict__ perm,
+             const int32_t* __restrict__ seg_start, const int32_t* __restrict__ seg_end,
+             const int32_t* __restrict__ item_off, unsigned long long* t64) {
+  constexpr int VPL = 16 / (int)sizeof(T);
+  __shared__ int2 red[kThreads * VPL];
+  const int S = (k + VPL - 1) / VPL;       // 16-byte column groups per row
+  const int R = kThreads / S;              // row groups
+  const int tid = threadIdx.x, slot = tid % S, g = tid / S;
+  const int32_t total = item_off[k];
+  for (int32_t item = blockIdx.x; item < total; item += gridDim.x) {
+    // center owning this item: last c with item_off[c] <= item
+    int lo = 0, hi = k;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (item_off[mid] <= item) lo = mid; else hi = mid;
+    }
+    const int32_t c = lo;
+    const int32_t r0 = seg_start[c] + (item - item_off[c]) * kChunk;
+    const int32_t r1 = min(seg_end[c], r0 + kChunk);
+    int32_t bt[VPL], bd[VPL];
+#pragma unroll
+    for (int q = 0; q < VPL; ++q) { bt[q] = kTInf; bd[q] = -1; }
+    if (g < R) {
+      int32_t p = r0 + g;
+      // kScanUnroll rows per step: independent 16-byte loads in flight
+      for (; p + (kScanUnroll - 1) * R < r1; p += kScanUnroll * R) {
+        int32_t d[kScanUnroll], own[kScanUnroll];
+        Vec16<T> x[kScanUnroll];
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; ++u) d[u] = min((uint32_t)perm[p + u * R], (uint32_t)(n - 1));
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; ++u) {
+          const T* rp = cm + (int64_t)d[u] * ld;
+          own[u] = (int32_t)rp[c];
+          x[u] = load16(rp + slot * VPL);
+        }
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; ++u) {
+#pragma unroll
+          for (int q = 0; q < VPL; ++q) {
+            const int32_t t = (int32_t)x[u].v[q] - own[u];
+            if (t < bt[q]) { bt[q] = t; bd[q] = d[u]; }
+          }
+        }
+      }
+      for (; p < r1; p += R) {
+        const int32_t d = min((uint32_t)perm[p], (uint32_t)(n - 1));
+        const T* rp = cm + (int64_t)d * ld;
+        const int32_t own = (int32_t)rp[c];
+        Vec16<T> x = load16(rp + slot * VPL);
+#pragma unroll
+        for (int q = 0; q < VPL; ++q) {
+          const int32_t t = (int32_t)x.v[q] - own;
+          if (t < bt[q]) { bt[q] = t; bd[q] = d; }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < VPL; ++q) red[g * S * VPL + slot * VPL + q] = make_int2(bt[q], bd[q]);
+    }
+    __syncthreads();
+    for (int col = tid; col < k; col += kThreads) {
+      int32_t t = kTInf, d = -1;
+      for (int gg = 0; gg < R; ++gg) {
+        const int2 e = red[gg * S * VPL + col];
+        if (lex_less(e.x, e.y, t, d)) { t = e.x; d = e.y; }
+      }
+      if (d >= 0 && col != c) {
+        const unsigned long long key =
+            ((unsigned long long)(uint32_t)(t + (int64_t)2147483648LL) << 32) | (uint32_t)d;
+        atomicMin(&t64[(int64_t)c * k + col], key);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) bt_unpack(const unsigned long long* __restrict__ t64,
+                                                      int32_t k, int32_t* tc, int32_t* td) {
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < (int64_t)k * k;
+       i += (int64_t)gridDim.x * kThreads) {
+    const unsigned long long e = t64[i];
+    if (e == ~0ull) {
+      tc[i] = kTInf;
+      td[i] = -1;
+    } else {
+      tc[i] = (int32_t)((int64_t)(e >> 32) - 2147483648LL);
+      td[i] = (int32_t)(e & 0xffffffffu);
+    }
+  }
+}
+
+int bt_max_k(int elem_bytes) { return kThreads * (16 / elem_bytes); }
+
+// Returns a cudaError_t (cudaSuccess on success); argument checks are done
+// by the caller.
+cudaError_t best_transfer_run(int32_t n, int32_t k, const void* cm, int elem_bytes, int64_t ld,
+                              const int32_t* assign, int32_t* tc, int32_t* td, void* ws,
+                              cudaStream_t st, int num_sms) {
+  void* base = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
+  BtWorkspace W = carve(base, n, k);
+  const int grid_lin = num_sms * 4;
+  bt_init_keys<<<grid_lin, kThreads, 0, st>>>(assign, n, k, W.k0, W.v0);
+  const int bits = 32 - __builtin_clz((unsigned)k);   // keys in [0, k]
+  const int passes = (bits + 7) / 8;
+  int32_t *sk = W.k0, *sv = W.v0, *dk = W.k1, *dv = W.v1;
+  for (int p = 0; p < passes; ++p) {
+    bt_hist<<<(unsigned)W.ntiles, kThreads, 0, st>>>(sk, n, 8 * p, W.tile_hist, W.ntiles);
+    bt_scan<<<1, kThreads, 0, st>>>(W.tile_hist, 256 * W.ntiles, nullptr);
+    bt_scatter<<<(unsigned)W.ntiles, kThreads, 0, st>>>(sk, sv, dk, dv, n, 8 * p, W.tile_hist,
+                                                        W.ntiles);
+    std::swap(sk, dk);
+    std::swap(sv, dv);
+  }
+  cudaMemsetAsync(W.seg_start, 0, 4ull * k, st);
+  cudaMemsetAsync(W.seg_end, 0, 4ull * k, st);
+  bt_bounds<<<grid_lin, kThreads, 0, st>>>(sk, n, k, W.seg_start, W.seg_end);
+  bt_items<<<grid_lin, kThreads, 0, st>>>(W.seg_start, W.seg_end, k, W.item_off, W.t64);
+  bt_scan<<<1, kThreads, 0, st>>>(W.item_off, k, W.item_off + k);
+  const int grid_scan = num_sms * 2;
+  if (elem_bytes == 2)
+    bt_scan_rows<int16_t><<<grid_scan, kThreads, 0, st>>>(
+        static_cast<const int16_t*>(cm), ld, n, k, sv, W.seg_start, W.seg_end, W.item_off, W.t64);
+  else
+    bt_scan_rows<int32_t><<<grid_scan, kThreads, 0, st>>>(
+        static_cast<const int32_t*>(cm), ld, n, k, sv, W.seg_start, W.seg_end, W.item_off, W.t64);
+  bt_unpack<<<grid_lin, kThreads, 0, st>>>(W.t64, k, tc, td);
+  return cudaGetLastError();
+}
+
+}  // namespace lbdd

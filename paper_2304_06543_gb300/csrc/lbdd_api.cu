@@ -1,0 +1,508 @@
+// Host side of the C ABI declared in include/lbdd.h.
+//
+// Owns device memory, validates inputs, picks launch shapes and launches the
+// kernels of asral_solver.cu and best_transfer.cu.  No solver arithmetic runs
+// on the host: every step of ASRAL executes in the CUDA kernels.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/lbdd.h"
+#include "lbdd_device.cuh"
+
+namespace lbdd {
+size_t solver_smem_bytes(int32_t k, int C, int elem_bytes);
+int solver_max_k(int C, int elem_bytes);
+int solver_max_clusters(int C, int elem_bytes, size_t smem);
+cudaError_t launch_solver(const DevInst* d_insts, int ninst, int* d_counter, int C,
+                          int nclusters, int elem_bytes, size_t smem, int flags,
+                          cudaStream_t st);
+size_t bt_workspace_bytes(int32_t n, int32_t k);
+int bt_max_k(int elem_bytes);
+cudaError_t best_transfer_run(int32_t n, int32_t k, const void* cm, int elem_bytes, int64_t ld,
+                              const int32_t* assign, int32_t* tc, int32_t* td, void* ws,
+                              cudaStream_t st, int num_sms);
+}  // namespace lbdd
+
+using namespace lbdd;
+
+struct lbdd_solver {
+  int32_t n = 0, k = 0;
+  int elem = 4;
+  int64_t ld = 0;
+  void* cm = nullptr;
+  int32_t *cap = nullptr, *pen = nullptr, *smin = nullptr, *order = nullptr,
+          *sort_tmp = nullptr, *assign = nullptr, *pos = nullptr, *load = nullptr,
+          *seg_size = nullptr, *page_tab = nullptr, *pool = nullptr, *free_stack = nullptr,
+          *tc = nullptr, *td = nullptr, *counter = nullptr;
+  int64_t* ctl = nullptr;
+  DevInst* d_inst = nullptr;
+  DevInst h_inst;
+  cudaStream_t st = nullptr;
+  int cluster = 0;         // 0 = auto
+  int ncyc_skip = 1;
+  int device = 0;
+  int num_sms = 0;
+  std::vector<void*> allocs;
+};
+
+static char g_cuda_err[256] = "no error";
+static std::mutex g_err_mu;
+
+static int cuda_fail(cudaError_t e, const char* what) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? LBDD_ERR_OOM : LBDD_ERR_CUDA;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+static int dev_alloc(lbdd_solver* s, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e, "cudaMalloc");
+  }
+  s->allocs.push_back(*p);
+  return LBDD_OK;
+}
+
+template <typename P>
+static int dalloc(lbdd_solver* s, P** p, size_t count) {
+  void* v = nullptr;
+  int rc = dev_alloc(s, &v, count * sizeof(P));
+  *p = static_cast<P*>(v);
+  return rc;
+}
+
+static void free_all(lbdd_solver* s) {
+  for (void* p : s->allocs) cudaFree(p);
+  s->allocs.clear();
+}
+
+static int check_device(int* dev, int* sms) {
+  CK(cudaGetDevice(dev));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, *dev));
+  if (prop.major != 10 || prop.minor != 3) return LBDD_ERR_NODEV;
+  *sms = prop.multiProcessorCount;
+  return LBDD_OK;
+}
+
+// ------------------------------------------------------------ CM ingest ---
+
+__global__ void cm_minmax(const void* cm, int elem, int64_t ld, int32_t n, int32_t k,
+                          int* out_min, int* out_max) {
+  int mn = INT32_MAX, mx = INT32_MIN;
+  const int64_t total = (int64_t)n * k;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = i / k, c = i - d * k;
+    const int v = elem == 2 ? (int)static_cast<const int16_t*>(cm)[d * ld + c]
+                            : static_cast<const int32_t*>(cm)[d * ld + c];
+    mn = min(mn, v);
+    mx = max(mx, v);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(out_min, mn);
+    atomicMax(out_max, mx);
+  }
+}
+
+__global__ void cm_narrow(const int32_t* src, int64_t lds, int16_t* dst, int64_t ldd, int32_t n,
+                          int32_t k) {
+  const int64_t total = (int64_t)n * k;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = i / k, c = i - d * k;
+    dst[d * ldd + c] = (int16_t)src[d * lds + c];
+  }
+}
+
+extern "C" int64_t lbdd_cm_pitch(int32_t k, int cm_dtype) {
+  const int vpl = cm_dtype == LBDD_CM_I16 ? 8 : 4;
+  return ((int64_t)k + vpl - 1) / vpl * vpl;
+}
+
+// Copy CM into padded device storage; returns storage, pitch and element size.
+static int ingest_cm(lbdd_solver* s, const void* cm, int dtype, int is_device) {
+  const int32_t n = s->n, k = s->k;
+  const int in_elem = dtype == LBDD_CM_I16 ? 2 : 4;
+  const int64_t ld = lbdd_cm_pitch(k, dtype);
+  const size_t bytes = ((size_t)n * ld + kColPad) * in_elem;
+  void* store = nullptr;
+  int rc = dev_alloc(s, &store, bytes);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(store, 0, bytes, s->st));
+  CK(cudaMemcpy2DAsync(store, ld * in_elem, cm, (size_t)k * in_elem, (size_t)k * in_elem, n,
+                       is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->st));
+  int* mm = nullptr;
+  rc = dalloc(s, &mm, 2);
+  if (rc) return rc;
+  int init[2] = {INT32_MAX, INT32_MIN};
+  CK(cudaMemcpyAsync(mm, init, sizeof(init), cudaMemcpyHostToDevice, s->st));
+  cm_minmax<<<s->num_sms * 4, 256, 0, s->st>>>(store, in_elem, ld, n, k, mm, mm + 1);
+  CK(cudaGetLastError());
+  int res[2];
+  CK(cudaMemcpyAsync(res, mm, sizeof(res), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  if (res[0] < 1) return LBDD_ERR_ARG;   // CM entries are positive integers
+  s->cm = store;
+  s->ld = ld;
+  s->elem = in_elem;
+  if (in_elem == 4 && res[1] <= INT16_MAX) {
+    const int64_t ld16 = lbdd_cm_pitch(k, LBDD_CM_I16);
+    void* narrow = nullptr;
+    rc = dev_alloc(s, &narrow, ((size_t)n * ld16 + kColPad) * 2);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(narrow, 0, ((size_t)n * ld16 + kColPad) * 2, s->st));
+    cm_narrow<<<s->num_sms * 8, 256, 0, s->st>>>(static_cast<const int32_t*>(store), ld,
+                                                 static_cast<int16_t*>(narrow), ld16, n, k);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->st));
+    // release the wide copy
+    CK(cudaFree(store));
+    s->allocs.erase(std::find(s->allocs.begin(), s->allocs.end(), store));
+    s->cm = narrow;
+    s->ld = ld16;
+    s->elem = 2;
+  }
+  return LBDD_OK;
+}
+
+// --------------------------------------------------------------- create ---
+
+static int pick_cluster(const lbdd_solver* s) {
+  if (s->cluster > 0) return s->cluster;
+  int C = (s->k + 63) / 64;
+  C = std::min(16, std::max(1, C));
+  // round up to a power of two for even column splits
+  int p = 1;
+  while (p < C) p <<= 1;
+  return std::min(16, p);
+}
+
+static int fits(const lbdd_solver* s, int C) {
+  const size_t smem = solver_smem_bytes(s->k, C, s->elem);
+  if (smem > 227 * 1024) return 0;
+  const int32_t w = (s->k + C - 1) / C;
+  if (w > solver_max_k(1, s->elem)) return 0;
+  return solver_max_clusters(C, s->elem, smem) >= 1;
+}
+
+extern "C" int lbdd_create(lbdd_solver** out, int32_t n, int32_t k, const void* cm, int cm_dtype,
+                           int cm_is_device, const int32_t* cap, const int32_t* pen,
+                           void* cuda_stream) {
+  if (!out) return LBDD_ERR_ARG;
+  *out = nullptr;
+  if (n < 1 || k < 1 || !cm || !cap || !pen) return LBDD_ERR_ARG;
+  if (cm_dtype != LBDD_CM_I32 && cm_dtype != LBDD_CM_I16) return LBDD_ERR_ARG;
+  for (int32_t i = 0; i < k; ++i)
+    if (cap[i] < 1 || pen[i] < 1) return LBDD_ERR_ARG;
+  lbdd_solver* s = new (std::nothrow) lbdd_solver();
+  if (!s) return LBDD_ERR_OOM;
+  s->st = static_cast<cudaStream_t>(cuda_stream);
+  int rc = check_device(&s->device, &s->num_sms);
+  if (rc) { delete s; return rc; }
+  rc = ingest_cm(s, cm, cm_dtype, cm_is_device);
+  if (rc) { free_all(s); delete s; return rc; }
+  if (solver_smem_bytes(k, 16, s->elem) > 227 * 1024) { free_all(s); delete s; return LBDD_ERR_ARG; }
+  const int32_t max_pages = (n + kPage - 1) / kPage;
+  const int32_t npages = max_pages + k;
+  if (!rc) rc = dalloc(s, &s->cap, k);
+  if (!rc) rc = dalloc(s, &s->pen, k);
+  if (!rc) rc = dalloc(s, &s->smin, n);
+  if (!rc) rc = dalloc(s, &s->order, n);
+  if (!rc) rc = dalloc(s, &s->sort_tmp, 3ull * n);
+  if (!rc) rc = dalloc(s, &s->assign, n);
+  if (!rc) rc = dalloc(s, &s->pos, n);
+  if (!rc) rc = dalloc(s, &s->load, k);
+  if (!rc) rc = dalloc(s, &s->seg_size, k);
+  if (!rc) rc = dalloc(s, &s->page_tab, (size_t)k * max_pages);
+  if (!rc) rc = dalloc(s, &s->pool, (size_t)npages * kPage);
+  if (!rc) rc = dalloc(s, &s->free_stack, npages);
+  if (!rc) rc = dalloc(s, &s->tc, (size_t)k * k);
+  if (!rc) rc = dalloc(s, &s->td, (size_t)k * k);
+  if (!rc) rc = dalloc(s, &s->ctl, CTL_COUNT);
+  if (!rc) rc = dalloc(s, &s->counter, 4);
+  if (!rc) rc = dalloc(s, &s->d_inst, 1);
+  if (rc) { free_all(s); delete s; return rc; }
+  DevInst& I = s->h_inst;
+  I.cm = s->cm; I.ld = s->ld; I.n = n; I.k = k; I.cap = s->cap; I.pen = s->pen;
+  I.smin = s->smin; I.order = s->order; I.sort_tmp = s->sort_tmp; I.assign = s->assign;
+  I.pos = s->pos; I.load = s->load; I.seg_size = s->seg_size; I.page_tab = s->page_tab;
+  I.pool = s->pool; I.free_stack = s->free_stack; I.tc = s->tc; I.td = s->td; I.ctl = s->ctl;
+  I.max_pages = max_pages; I.npages = npages;
+  auto fail = [&](cudaError_t e, const char* w) { int r = cuda_fail(e, w); free_all(s); delete s; return r; };
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(s->cap, cap, 4ull * k, cudaMemcpyHostToDevice, s->st))) return fail(e, "cap");
+  if ((e = cudaMemcpyAsync(s->pen, pen, 4ull * k, cudaMemcpyHostToDevice, s->st))) return fail(e, "pen");
+  if ((e = cudaMemsetAsync(s->ctl, 0, sizeof(int64_t) * CTL_COUNT, s->st))) return fail(e, "ctl");
+  if ((e = cudaMemsetAsync(s->assign, 0xff, 4ull * n, s->st))) return fail(e, "assign");
+  if ((e = cudaMemsetAsync(s->load, 0, 4ull * k, s->st))) return fail(e, "load");
+  // defined contents everywhere, so that a corrupt index can never leave the pool
+  if ((e = cudaMemsetAsync(s->page_tab, 0, 4ull * k * max_pages, s->st))) return fail(e, "pages");
+  if ((e = cudaMemsetAsync(s->pool, 0, 4ull * npages * kPage, s->st))) return fail(e, "pool");
+  if ((e = cudaMemsetAsync(s->pos, 0, 4ull * n, s->st))) return fail(e, "pos");
+  if ((e = cudaMemcpyAsync(s->d_inst, &I, sizeof(DevInst), cudaMemcpyHostToDevice, s->st))) return fail(e, "inst");
+  if ((e = cudaStreamSynchronize(s->st))) return fail(e, "sync");
+  *out = s;
+  return LBDD_OK;
+}
+
+extern "C" int lbdd_set_option(lbdd_solver* s, int option, int64_t value) {
+  if (!s) return LBDD_ERR_ARG;
+  switch (option) {
+    case LBDD_OPT_CLUSTER:
+      if (value < 0 || value > 16) return LBDD_ERR_ARG;
+      if (value > 0 && !fits(s, (int)value)) return LBDD_ERR_ARG;
+      s->cluster = (int)value;
+      return LBDD_OK;
+    case LBDD_OPT_NCYC_SKIP:
+      if (value != 0 && value != 1) return LBDD_ERR_ARG;
+      s->ncyc_skip = (int)value;
+      return LBDD_OK;
+    default:
+      return LBDD_ERR_ARG;
+  }
+}
+
+// ---------------------------------------------------------------- solve ---
+
+static int status_to_rc(int64_t st) {
+  if (st == 0) return LBDD_OK;
+  if (st == ST_ERR_INVARIANT) return LBDD_ERR_INVARIANT;
+  return LBDD_ERR_STATE;
+}
+
+static int set_target(lbdd_solver* s, int64_t max_rounds, cudaStream_t st) {
+  int64_t h[2];
+  CK(cudaMemcpyAsync(h, s->ctl + CTL_ROUNDS, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h + 1, s->ctl + CTL_STATUS, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h[1] != 0) return LBDD_ERR_STATE;
+  const int64_t target = max_rounds < 0 ? (int64_t)s->n : std::min<int64_t>(s->n, h[0] + max_rounds);
+  CK(cudaMemcpyAsync(s->ctl + CTL_TARGET, &target, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return LBDD_OK;
+}
+
+static int choose_cluster(lbdd_solver* s) {
+  int C = pick_cluster(s);
+  while (C > 1 && !fits(s, C)) C >>= 1;
+  return fits(s, C) ? C : 0;
+}
+
+extern "C" int lbdd_solve(lbdd_solver* s, int64_t max_rounds) {
+  if (!s) return LBDD_ERR_ARG;
+  int rc = set_target(s, max_rounds, s->st);
+  if (rc) return rc;
+  const int C = choose_cluster(s);
+  if (C < 1) return LBDD_ERR_ARG;
+  const size_t smem = solver_smem_bytes(s->k, C, s->elem);
+  CK(cudaMemsetAsync(s->counter, 0, sizeof(int32_t), s->st));
+  CK(launch_solver(s->d_inst, 1, s->counter, C, 1, s->elem, smem,
+                   s->ncyc_skip ? 0 : OPT_NO_NCYC_SKIP, s->st));
+  int64_t st = 0;
+  CK(cudaMemcpyAsync(&st, s->ctl + CTL_STATUS, sizeof(int64_t), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return status_to_rc(st);
+}
+
+extern "C" int lbdd_reset(lbdd_solver* s) {
+  if (!s) return LBDD_ERR_ARG;
+  CK(cudaMemsetAsync(s->ctl, 0, sizeof(int64_t) * CTL_COUNT, s->st));
+  CK(cudaMemsetAsync(s->assign, 0xff, 4ull * s->n, s->st));
+  CK(cudaMemsetAsync(s->load, 0, 4ull * s->k, s->st));
+  return LBDD_OK;
+}
+
+extern "C" int lbdd_solve_batch(lbdd_solver* const* solvers, int m, int64_t max_rounds,
+                                int cluster_size, int max_clusters, void* stream) {
+  if (!solvers || m < 1 || cluster_size < 0 || cluster_size > 16 || max_clusters < 0)
+    return LBDD_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < m; ++i) {
+    if (!solvers[i]) return LBDD_ERR_ARG;
+    int rc = set_target(solvers[i], max_rounds, st);
+    if (rc) return rc;
+  }
+  int flags = 0;
+  for (int i = 0; i < m; ++i)
+    if (!solvers[i]->ncyc_skip) flags = OPT_NO_NCYC_SKIP;
+  // one persistent launch per element size, largest instances first
+  for (int elem : {2, 4}) {
+    std::vector<lbdd_solver*> group;
+    for (int i = 0; i < m; ++i)
+      if (solvers[i]->elem == elem) group.push_back(solvers[i]);
+    if (group.empty()) continue;
+    std::stable_sort(group.begin(), group.end(), [](const lbdd_solver* a, const lbdd_solver* b) {
+      return (int64_t)a->n * a->k > (int64_t)b->n * b->k;
+    });
+    int32_t kmax = 0;
+    for (auto* g : group) kmax = std::max(kmax, g->k);
+    int C = cluster_size;
+    if (C == 0) {
+      C = 1;
+      while (C < 16 && (kmax + C - 1) / C > 512) C <<= 1;
+    }
+    const size_t smem = solver_smem_bytes(kmax, C, elem);
+    if (smem > 227 * 1024 || (kmax + C - 1) / C > solver_max_k(1, elem)) return LBDD_ERR_ARG;
+    const int fit = solver_max_clusters(C, elem, smem);
+    if (fit < 1) return LBDD_ERR_ARG;
+    int ncl = std::min<int>((int)group.size(), fit);
+    if (max_clusters > 0) ncl = std::min(ncl, max_clusters);
+    std::vector<DevInst> h;
+    for (auto* g : group) h.push_back(g->h_inst);
+    DevInst* d = nullptr;
+    int32_t* counter = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(DevInst) * h.size(), st));
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&counter), sizeof(int32_t), st));
+    CK(cudaMemcpyAsync(d, h.data(), sizeof(DevInst) * h.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
+    CK(launch_solver(d, (int)h.size(), counter, C, ncl, elem, smem, flags, st));
+    CK(cudaFreeAsync(d, st));
+    CK(cudaFreeAsync(counter, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  int first = LBDD_OK;
+  for (int i = 0; i < m; ++i) {
+    int64_t v = 0;
+    CK(cudaMemcpy(&v, solvers[i]->ctl + CTL_STATUS, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    int rc = status_to_rc(v);
+    if (rc && first == LBDD_OK) first = rc;
+  }
+  return first;
+}
+
+// ------------------------------------------------------------ accessors ---
+
+static int read_ctl(const lbdd_solver* s, int idx, int64_t* out) {
+  CK(cudaMemcpyAsync(out, s->ctl + idx, sizeof(int64_t), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return LBDD_OK;
+}
+
+extern "C" int lbdd_objective(const lbdd_solver* s, int64_t* out) {
+  if (!s || !out) return LBDD_ERR_ARG;
+  return read_ctl(s, CTL_DELTA, out);
+}
+
+extern "C" int lbdd_rounds_done(const lbdd_solver* s, int64_t* out) {
+  if (!s || !out) return LBDD_ERR_ARG;
+  return read_ctl(s, CTL_ROUNDS, out);
+}
+
+extern "C" int lbdd_assignment(const lbdd_solver* s, int32_t* out, int out_is_device) {
+  if (!s || !out) return LBDD_ERR_ARG;
+  CK(cudaMemcpyAsync(out, s->assign, 4ull * s->n,
+                     out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return LBDD_OK;
+}
+
+extern "C" int lbdd_loads(const lbdd_solver* s, int32_t* out) {
+  if (!s || !out) return LBDD_ERR_ARG;
+  CK(cudaMemcpyAsync(out, s->load, 4ull * s->k, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return LBDD_OK;
+}
+
+extern "C" int lbdd_get_stats(const lbdd_solver* s, lbdd_stats* out) {
+  if (!s || !out) return LBDD_ERR_ARG;
+  int64_t c[CTL_COUNT];
+  CK(cudaMemcpyAsync(c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  out->rounds = c[CTL_ROUNDS];
+  out->cycles_applied = c[CTL_CYCLES];
+  out->paths_applied = c[CTL_PATHS];
+  out->bf_calls = c[CTL_BF_CALLS];
+  out->bf_sweeps = c[CTL_BF_SWEEPS];
+  out->bf_max_sweeps = c[CTL_BF_MAX];
+  out->moves = c[CTL_MOVES];
+  out->ncyc_skipped = c[CTL_NCYC_SKIPPED];
+  out->rows_scanned = c[CTL_ROWS_SCANNED];
+  out->cm_elem_bytes = s->elem;
+  out->cluster_size = const_cast<lbdd_solver*>(s)->cluster ? s->cluster
+                                                            : choose_cluster(const_cast<lbdd_solver*>(s));
+  return LBDD_OK;
+}
+
+extern "C" int lbdd_best_transfer_table(const lbdd_solver* s, int32_t* tc, int32_t* td,
+                                        int out_is_device) {
+  if (!s || !tc || !td) return LBDD_ERR_ARG;
+  const cudaMemcpyKind kind = out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpyAsync(tc, s->tc, 4ull * s->k * s->k, kind, s->st));
+  CK(cudaMemcpyAsync(td, s->td, 4ull * s->k * s->k, kind, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return LBDD_OK;
+}
+
+extern "C" int lbdd_solver_cm(const lbdd_solver* s, const void** cm_dev, int* cm_dtype,
+                              int64_t* ld) {
+  if (!s || !cm_dev || !cm_dtype || !ld) return LBDD_ERR_ARG;
+  *cm_dev = s->cm;
+  *cm_dtype = s->elem == 2 ? LBDD_CM_I16 : LBDD_CM_I32;
+  *ld = s->ld;
+  return LBDD_OK;
+}
+
+extern "C" void lbdd_destroy(lbdd_solver* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->st);
+  free_all(s);
+  delete s;
+}
+
+extern "C" const char* lbdd_strerror(int code) {
+  switch (code) {
+    case LBDD_OK: return "ok";
+    case LBDD_ERR_ARG: return "invalid argument";
+    case LBDD_ERR_OOM: return "out of memory";
+    case LBDD_ERR_CUDA: return "CUDA runtime error";
+    case LBDD_ERR_TIMEOUT: return "timed out";
+    case LBDD_ERR_INVARIANT: return "invariant violated (negative cycle in Gamma)";
+    case LBDD_ERR_STATE: return "invalid state";
+    case LBDD_ERR_NODEV: return "no compute capability 10.3 device";
+    case LBDD_ERR_BUDGET: return "request exceeds the memory budget";
+    default: return "unknown status";
+  }
+}
+
+extern "C" const char* lbdd_last_cuda_error(void) { return g_cuda_err; }
+
+// ----------------------------------------------------- best transfer K2 ---
+
+extern "C" size_t lbdd_best_transfer_workspace(int32_t n, int32_t k) {
+  return bt_workspace_bytes(n, k);
+}
+
+extern "C" int lbdd_best_transfer(int32_t n, int32_t k, const void* cm_dev, int cm_dtype,
+                                  int64_t ld, const int32_t* assign_dev, int32_t* tc_dev,
+                                  int32_t* td_dev, void* workspace, size_t workspace_bytes,
+                                  void* stream) {
+  if (n < 1 || k < 1 || !cm_dev || !assign_dev || !tc_dev || !td_dev || !workspace)
+    return LBDD_ERR_ARG;
+  if (cm_dtype != LBDD_CM_I32 && cm_dtype != LBDD_CM_I16) return LBDD_ERR_ARG;
+  const int elem = cm_dtype == LBDD_CM_I16 ? 2 : 4;
+  if (ld < k || (ld * elem) % 16 != 0 || (reinterpret_cast<uintptr_t>(cm_dev) & 15) != 0)
+    return LBDD_ERR_ARG;
+  if (k > bt_max_k(elem)) return LBDD_ERR_ARG;
+  if (workspace_bytes < bt_workspace_bytes(n, k)) return LBDD_ERR_ARG;
+  int dev = 0, sms = 0;
+  int rc = check_device(&dev, &sms);
+  if (rc) return rc;
+  CK(best_transfer_run(n, k, cm_dev, elem, ld, assign_dev, tc_dev, td_dev, workspace,
+                       static_cast<cudaStream_t>(stream), sms));
+  return LBDD_OK;
+}

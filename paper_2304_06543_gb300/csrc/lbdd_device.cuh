@@ -1,0 +1,145 @@
+// Internal device-side definitions of the LBDD/ASRAL CUDA path (sm_103a).
+//
+// Everything here is private to the library: the public boundary is the C ABI
+// in include/lbdd.h.  All arithmetic is integer.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbdd {
+
+constexpr int kThreads = 512;          // threads per CTA of every kernel here
+constexpr int kWarps = kThreads / 32;
+constexpr int kPageShift = 8;          // member lists are paged, 256 units/page
+constexpr int kPage = 1 << kPageShift;
+constexpr int kMaxCluster = 16;        // cluster sizes 1..16 (16 is non-portable)
+constexpr int32_t kTInf = INT32_MAX;   // best-transfer entry of an empty segment
+constexpr int64_t kDInf = (int64_t)1 << 62;  // unreached Bellman-Ford label
+constexpr int kColPad = 128;           // CM allocation slack for vector over-reads
+
+// Per-instance control words (int64, device memory).
+enum CtlIndex {
+  CTL_ROUNDS = 0,      // rounds completed
+  CTL_DELTA,           // tracked objective, Eq. (1)
+  CTL_FREE_TOP,        // free-page stack height
+  CTL_STATUS,          // 0 = ok, else an LBDD_ERR_* code
+  CTL_PROLOGUE,        // 1 once s_min/order/state are initialised
+  CTL_TARGET,          // rounds to reach in the current launch
+  CTL_CYCLES,          // negative cycles applied (Alg. 2)
+  CTL_PATHS,           // negative paths applied (Alg. 3)
+  CTL_BF_CALLS,        // Bellman-Ford calls actually run
+  CTL_BF_SWEEPS,       // total synchronous sweeps
+  CTL_BF_MAX,          // longest call, in sweeps
+  CTL_MOVES,           // unit transfers
+  CTL_NCYC_SKIPPED,    // NegCycle calls skipped because T[j] did not change
+  CTL_ROWS_SCANNED,    // CM rows read by segment rescans
+  CTL_MAXKEY,          // largest CM(d, s_min(d)) (radix-sort width)
+  CTL_COUNT
+};
+
+// Status codes shared with include/lbdd.h.
+enum : int64_t {
+  ST_OK = 0,
+  ST_ERR_INVARIANT = -5,
+};
+
+// Launch-wide option bits.
+enum : int {
+  OPT_NO_NCYC_SKIP = 1,   // always run the NegCycle Bellman-Ford
+};
+
+// Device view of one instance.  Pointers are device memory owned by the
+// library (lbdd_solver).
+struct DevInst {
+  const void* cm;       // n x ld, int32 or int16, demand-major, padded rows
+  int64_t ld;           // row pitch in elements (multiple of 16 bytes)
+  int32_t n, k;
+  const int32_t* cap;   // k
+  const int32_t* pen;   // k
+  int32_t* smin;        // n: most suitable center
+  int32_t* order;       // n: MinDistance extraction order
+  int32_t* sort_tmp;    // 3n: radix-sort scratch
+  int32_t* assign;      // n: center of each unit, -1 before its round
+  int32_t* pos;         // n: index of the unit inside its center's list
+  int32_t* load;        // k: units allotted per center
+  int32_t* seg_size;    // k: length of each member list
+  int32_t* page_tab;    // k x max_pages: page ids of each member list
+  int32_t* pool;        // pages x kPage member slots
+  int32_t* free_stack;  // pages
+  int32_t* tc;          // k x k best-transfer cost (row u = from u)
+  int32_t* td;          // k x k best-transfer unit
+  int64_t* ctl;         // CTL_COUNT
+  int32_t max_pages;    // per center
+  int32_t npages;       // in the pool
+};
+
+// ------------------------------------------------------------ cluster ops ---
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_nrank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_index() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// Full cluster barrier; every thread of every CTA of the cluster must reach
+// it.  Release/acquire order shared and global memory across the cluster.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n\t"
+      "barrier.cluster.wait.acquire.aligned;\n\t" ::: "memory");
+}
+// Address of `p` (a shared variable of this CTA) in CTA `rank`'s window.
+__device__ __forceinline__ uint32_t dsmem_addr(const void* p, uint32_t rank) {
+  uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p)), r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ int32_t dsmem_ld32(uint32_t addr) {
+  int32_t v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ int64_t dsmem_ld64(uint32_t addr) {
+  int64_t v;
+  asm volatile("ld.shared::cluster.s64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+// ------------------------------------------------------------ CM access ---
+
+template <typename T>
+struct Vec16 {
+  static constexpr int N = 16 / sizeof(T);
+  T v[N];
+};
+
+template <typename T>
+__device__ __forceinline__ Vec16<T> load16(const T* p) {
+  Vec16<T> r;
+  int4 x = __ldg(reinterpret_cast<const int4*>(p));
+  static_assert(sizeof(r) == sizeof(x), "vector size");
+  *reinterpret_cast<int4*>(&r) = x;
+  return r;
+}
+
+// Lexicographic (cost, unit) order used for every best-transfer entry.
+__device__ __forceinline__ bool lex_less(int32_t c, int32_t d, int32_t bc, int32_t bd) {
+  return c < bc || (c == bc && (uint32_t)d < (uint32_t)bd);
+}
+
+}  // namespace lbdd

@@ -1,0 +1,65 @@
+"""The C-ABI library builds, loads and exports every symbol of include/lbdd.h.
+
+CPU only: no call here reaches a kernel (argument checks and host-side
+helpers only).
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbdd.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(lbdd_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2304_06543_gb300 as lb
+    return lb.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_built_for_sm_103a():
+    import paper_2304_06543_gb300._build as b
+    assert "arch=compute_103a,code=sm_103a" in " ".join(b.ARCH)
+    assert os.path.exists(b.LIB)
+
+
+def test_host_side_calls(lib):
+    import paper_2304_06543_gb300 as lb
+    assert lb.strerror(0) == "ok"
+    assert "invariant" in lb.strerror(-5)
+    assert lb.cm_pitch(500, lb.CM_I16) == 504
+    assert lb.cm_pitch(501, lb.CM_I32) == 504
+    assert lb.best_transfer_workspace(0, 5) == 0
+    h = ctypes.c_void_p()
+    # argument errors are reported before any CUDA call
+    assert lib.lbdd_create(ctypes.byref(h), 0, 5, None, 0, 0, None, None, None) == lb.ERR_ARG
+    assert h.value is None
+    assert lib.lbdd_solve(None, -1) == lb.ERR_ARG
+    lib.lbdd_destroy(None)
+
+
+def test_product_does_not_reference_oracle():
+    """The CUDA path and its binding never import or link the oracle."""
+    pkg = os.path.join(ROOT, "paper_2304_06543_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src
+                assert "asral_oracle" not in src and "_oracle.so" not in src
