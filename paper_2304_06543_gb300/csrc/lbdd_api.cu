@@ -211,6 +211,8 @@ extern "C" int lbdd_create(lbdd_solver** out, int32_t n, int32_t k, const void* 
     if (cap[i] < 1 || pen[i] < 1) return LBDD_ERR_ARG;
   lbdd_solver* s = new (std::nothrow) lbdd_solver();
   if (!s) return LBDD_ERR_OOM;
+  s->n = n;
+  s->k = k;
   s->st = static_cast<cudaStream_t>(cuda_stream);
   int rc = check_device(&s->device, &s->num_sms);
   if (rc) { delete s; return rc; }
