@@ -6,11 +6,11 @@
  * S = {s_0..s_{k-1}}, demand units D = {d_0..d_{n-1}}, a cost matrix CM
  * (n x k, positive integers, Table 1 and the cost-matrix definition of
  * Section 2), a positive integer capacity c_s per center and a penalty q_s
- * per center (Def. 3; here the constant per-unit form of the paper's
+ * per center (Def. 4; here the constant per-unit form of the paper's
  * experiments, Section 5: every unit beyond c_s costs pen[s]), find a
  * complete allotment minimising Eq. (1):
  *     sum_d CM(d, a(d)) + sum_s pen[s] * max(0, load_s - c_s).
- * The solver runs ASRAL (Alg. 1 with Alg. 2 and Alg. 3) with canonical
+ * The solver runs ASRAL (Alg. 2 with Alg. 1 and Alg. 4) with canonical
  * tie-breaking, so its output is one deterministic allotment that equals the
  * project's CPU oracle bit for bit.
  *
@@ -57,26 +57,45 @@ typedef enum lbdd_cm_dtype {
 typedef struct lbdd_solver lbdd_solver;   /* opaque, owned by the library */
 
 typedef struct lbdd_stats {
-  int64_t rounds;           /* rounds of Alg. 1 completed */
-  int64_t cycles_applied;   /* negative cycles removed (Alg. 2) */
-  int64_t paths_applied;    /* negative paths removed (Alg. 3) */
+  int64_t rounds;           /* rounds of Alg. 2 completed */
+  int64_t cycles_applied;   /* negative cycles removed (Alg. 1) */
+  int64_t paths_applied;    /* negative paths removed (Alg. 4) */
   int64_t bf_calls;         /* Bellman-Ford runs to convergence */
   int64_t bf_sweeps;        /* synchronous sweeps over all those runs */
   int64_t bf_max_sweeps;    /* longest run, in sweeps */
   int64_t moves;            /* demand units transferred between centers */
-  int64_t ncyc_skipped;     /* Alg. 2 calls answered without Bellman-Ford because
+  int64_t ncyc_skipped;     /* Alg. 1 calls answered without Bellman-Ford because
                                the new unit lowered no best-transfer cost */
   int64_t rows_scanned;     /* CM rows read by best-transfer segment rescans */
   int64_t cm_elem_bytes;    /* 2 or 4: element size of the stored CM */
   int64_t cluster_size;     /* CTAs per thread-block cluster used by solves */
+  /* Device-side phase timers of the cluster's first CTA, nanoseconds summed
+     over all launches (tracing aid; phases overlap barriers of other CTAs). */
+  int64_t prologue_ns;      /* s_min + MinDistance order + state init */
+  int64_t rounds_ns;        /* whole round loop */
+  int64_t merge_ns;         /* allotment + merge of the new unit's row */
+  int64_t relax_ns;         /* Bellman-Ford relaxation of owned columns */
+  int64_t sync_ns;          /* Bellman-Ford cluster barriers */
+  int64_t gather_ns;        /* Bellman-Ford exchange of label changes */
+  int64_t apply_ns;         /* path application (member lists, loads) */
+  int64_t rescan_ns;        /* segment rescans of the best-transfer rows */
+  int64_t npath_reused;     /* Alg. 4 calls answered from the labels of an Alg. 1
+                               Bellman-Ford that applied nothing (exact: same graph
+                               except for the sink edges) */
+  int64_t col_rows;         /* member rows read by column-subset rescans */
+  int64_t front_sum;        /* sum over sweeps of the Bellman-Ford frontier size */
+  int64_t front_hist[6];    /* sweeps with frontier 1, 2-4, 5-16, 17-64, 65-256, >256 */
 } lbdd_stats;
 
 /* Options for lbdd_set_option. */
 typedef enum lbdd_option {
   LBDD_OPT_CLUSTER = 1,     /* CTAs per cluster for lbdd_solve, 1..16 (0 = auto) */
-  LBDD_OPT_NCYC_SKIP = 2,   /* 1 (default): skip Alg. 2's Bellman-Ford when the new
+  LBDD_OPT_NCYC_SKIP = 2,   /* 1 (default): skip Alg. 1's Bellman-Ford when the new
                                unit lowers no best-transfer cost (exact by Lemma 1);
                                0: always run it */
+  LBDD_OPT_NPATH_REUSE = 3, /* 1 (default): answer Alg. 4 from the converged labels of
+                               an Alg. 1 run that applied nothing; 0: always run a
+                               separate Bellman-Ford */
 } lbdd_option;
 
 /* Create a solver for one LBDD instance (Section 2.1 inputs).
@@ -96,7 +115,7 @@ int lbdd_create(lbdd_solver** out, int32_t n, int32_t k, const void* cm, int cm_
 /* Set an lbdd_option; LBDD_ERR_ARG for an unknown option or bad value. */
 int lbdd_set_option(lbdd_solver* s, int option, int64_t value);
 
-/* Run rounds of Alg. 1 (each: allot the next unit of the MinDistance order
+/* Run rounds of Alg. 2 (each: allot the next unit of the MinDistance order
  * to its most suitable center, Negative Cycle Refinement at that center,
  * and Negative Path Refinement if the center was full).  max_rounds < 0
  * runs to completion (n rounds in total); otherwise at most max_rounds more
@@ -106,7 +125,7 @@ int lbdd_set_option(lbdd_solver* s, int option, int64_t value);
 int lbdd_solve(lbdd_solver* s, int64_t max_rounds);
 
 /* Forget all progress: the next lbdd_solve starts again from round 0 on the
- * CM already resident on the device (the prologue of Alg. 1 is redone).
+ * CM already resident on the device (the prologue of Alg. 2 is redone).
  * Stream-ordered; no host synchronisation. */
 int lbdd_reset(lbdd_solver* s);
 
@@ -120,7 +139,7 @@ int lbdd_reset(lbdd_solver* s);
 int lbdd_solve_batch(lbdd_solver* const* solvers, int m, int64_t max_rounds,
                      int cluster_size, int max_clusters, void* stream);
 
-/* Tracked objective Delta of Alg. 1 (equals Eq. (1) of the current
+/* Tracked objective Delta of Alg. 2 (equals Eq. (1) of the current
  * allotment).  out: host pointer. */
 int lbdd_objective(const lbdd_solver* s, int64_t* out);
 
@@ -137,7 +156,7 @@ int lbdd_rounds_done(const lbdd_solver* s, int64_t* out);
 /* Counters of the solve so far (host struct). */
 int lbdd_get_stats(const lbdd_solver* s, lbdd_stats* out);
 
-/* Copy the solver's best-transfer table (Defs. 4-6: for every ordered pair
+/* Copy the solver's best-transfer table (Defs. 8-10: for every ordered pair
  * (u, v), the cheapest transfer of a unit allotted to u over to v):
  * tc[u*k+v] = CM(d,v) - CM(d,u) of the lexicographically smallest
  * (cost, d), INT32_MAX if u holds no unit or u == v; td[u*k+v] = that d or

@@ -125,7 +125,7 @@ def objective(cm, cap, pen, assign) -> int:
 
 
 def asral(cm, cap, pen, mode=MODE_HEAP, max_rounds=-1, check=False) -> Result:
-    """Alg. 1 on the instance; see asral_oracle.c for the exact reading."""
+    """Alg. 2 on the instance; see asral_oracle.c for the exact reading."""
     cm = _c(cm, np.int32)
     n, k = cm.shape
     cap = _c(cap, np.int32)

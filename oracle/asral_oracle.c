@@ -13,23 +13,24 @@
  * j-th unit beyond capacity costs pen[s] for every j >= 1.
  *
  * Readings where the paper is silent or loose (all documented in DESIGN):
- *  - "ties are broken arbitrarily" (Defs. 5 and 6): the best-transfer edge
+ *  - "ties are broken arbitrarily" (Defs. 9 and 10): the best-transfer edge
  *    u->v is the lexicographic minimum of (transfer cost, demand index);
  *  - "most suitable" center (Section 3.1): lowest index among the minima;
  *    MinDistance heap order: (CM(d, s_min(d)), d) ascending;
- *  - Bellman-Ford (Sections 3.3/3.4, Alg. 4): synchronous sweeps over all
+ *  - Bellman-Ford (Sections 3.3/3.4, Alg. 3): synchronous sweeps over all
  *    nodes, a label changes only on strict improvement, the parent is the
  *    lowest-index predecessor achieving the new label, stop at the first
  *    sweep with no change; a change at sweep N (N = node count) means a
  *    negative cycle, i.e. a broken Lemma 1/2, reported as an error;
- *  - Def. 5 (d) "all other edges have 0 cost" adds no edge: the only pair it
+ *  - Def. 9 (d) "all other edges have 0 cost" adds no edge: the only pair it
  *    could concern that matters is anchor-out -> anchor-in, the empty cycle,
- *    whose cost 0 is rejected by the "< 0" test of Alg. 2;
- *  - Alg. 2 line 8 comment and Alg. 3 line 10: the objective changes by the
+ *    whose cost 0 is rejected by the "< 0" test of Alg. 1;
+ *  - the objective updates inside Alg. 1 and Alg. 4 (the in-loop comment and
+ *    the extra "cost of last edge" update of Alg. 4): the objective changes by the
  *    path cost exactly once (transfer edges CM(new) - CM(old), plus the
  *    penalty edge for a negative path);
- *  - Def. 6 (c): q_u() is pen[u] when u is at or above capacity, else 0;
- *    q_{s*}() is pen[s*] (s* is over capacity whenever Alg. 3 runs).
+ *  - Def. 10 (c): q_u() is pen[u] when u is at or above capacity, else 0;
+ *    q_{s*}() is pen[s*] (s* is over capacity whenever Alg. 4 runs).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -78,7 +79,7 @@ int64_t oracle_objective(int64_t n, int64_t k, const int32_t *cm, const int32_t 
 }
 
 /* ------------------------------------------------------------------------
- * Alg. 1 line 1 (and Section 3.1): the "most suitable" center of every unit
+ * Alg. 2, first step (and Section 3.1): the "most suitable" center of every unit
  * (lowest index among the minima of its CM row), and the MinDistance heap's
  * extraction order, realised as a sort of (CM(d, s_min), d) ascending.
  */
@@ -109,8 +110,8 @@ int oracle_smin_order(int64_t n, int64_t k, const int32_t *cm, int32_t *smin, in
 }
 
 /* ------------------------------------------------------------------------
- * Best-transfer table by definition (Def. 4 with the min taken per ordered
- * pair as in Defs. 5/6 (a)): for every ordered pair (u, v), u != v, the
+ * Best-transfer table by definition (Def. 8 with the min taken per ordered
+ * pair as in Defs. 9/10 (a)): for every ordered pair (u, v), u != v, the
  * lexicographically smallest (CM(d,v) - CM(d,u), d) over the units d
  * allotted to u.  tc = OR_INF and td = -1 when u has no unit.
  */
@@ -135,7 +136,7 @@ int oracle_best_transfer(int64_t n, int64_t k, const int32_t *cm, const int32_t 
 }
 
 /* ------------------------------------------------------------------------
- * Bellman-Ford label-correcting shortest paths (Sections 3.3/3.4; Alg. 4 is
+ * Bellman-Ford label-correcting shortest paths (Sections 3.3/3.4; Alg. 3 is
  * the same relaxation with the sweep run on a GPU).  Synchronous form: each
  * sweep computes every label from the previous sweep's labels.
  *   W: N x N, W[u*N+v] = edge cost or OR_INF for "no edge".
@@ -254,8 +255,8 @@ typedef struct {
     oracle_stats st;
 } asral;
 
-/* Push the k-1 transfer edges of unit d, now allotted to center a (Alg. 1
- * line 6, Alg. 2/3 line 6 "Update Gamma DS"). */
+/* Push the k-1 transfer edges of unit d, now allotted to center a (the
+ * "Update Gamma DS" steps of Alg. 2, Alg. 1 and Alg. 4). */
 static int heap_add_unit(asral *S, int32_t d, int32_t a) {
     for (int64_t v = 0; v < S->k; ++v) {
         if (v == a) continue;
@@ -289,7 +290,7 @@ static int refresh_table(asral *S) {
     return OR_OK;
 }
 
-/* NegCycle graph NCyc(Gamma(A), j), Def. 5.  Node u < k is center u; the
+/* NegCycle graph NCyc(Gamma(A), j), Def. 9.  Node u < k is center u; the
  * anchor j plays s*out (the source) and node k is s*in (the sink).
  *  (a) u, v not the anchor: best transfer u -> v;
  *  (b) s*out -> v: best transfer j -> v;
@@ -307,7 +308,7 @@ static void build_ncyc(asral *S, int32_t j) {
     }
 }
 
-/* NegPath graph NPath(Gamma(B3), j), Def. 6.  Transfer edges as in (a)/(b);
+/* NegPath graph NPath(Gamma(B3), j), Def. 10.  Transfer edges as in (a)/(b);
  * (c) u -> s*in costs q_u() - q_{s*}(): the penalty of one more unit at u
  * (pen[u] if u is at or above capacity, else 0) minus the penalty saved at
  * the overloaded anchor (pen[j]); (d) self loops cost 0 and are omitted
@@ -346,7 +347,7 @@ static int64_t extract_path(asral *S, int32_t src) {
     return len; /* path[0] = src, path[len] = sink */
 }
 
-/* Apply the transfers of a path (Alg. 2 lines 5-9, Alg. 3 lines 5-9).  All
+/* Apply the transfers of a path (the "cost < 0" branch of Alg. 1 and Alg. 4).  All
  * moved units are read from the table snapshot before any move.  For NCyc
  * the edge into the sink moves a unit into the anchor j; for NPath that edge
  * is the penalty edge and moves nothing.  Returns the terminal center of a
@@ -377,7 +378,7 @@ static int apply_path(asral *S, int64_t len, int32_t j, int is_npath, int32_t *t
     return OR_OK;
 }
 
-/* Alg. 2 (Negative Cycle Refinement) with anchor j. */
+/* Alg. 1 (Negative Cycle Refinement) with anchor j. */
 static int negcycle_refine(asral *S, int32_t j) {
     int rc = refresh_table(S);
     if (rc) return rc;
@@ -401,7 +402,7 @@ static int negcycle_refine(asral *S, int32_t j) {
     return OR_OK;
 }
 
-/* Alg. 3 (Negative Path Refinement) with the overloaded anchor j. */
+/* Alg. 4 (Negative Path Refinement) with the overloaded anchor j. */
 static int negpath_refine(asral *S, int32_t j) {
     int rc = refresh_table(S);
     if (rc) return rc;
@@ -489,7 +490,7 @@ static void asral_free(asral *S) {
 }
 
 /* ------------------------------------------------------------------------
- * Alg. 1 (ASRAL).  Runs `max_rounds` rounds (or all n if max_rounds < 0) of:
+ * Alg. 2 (ASRAL).  Runs `max_rounds` rounds (or all n if max_rounds < 0) of:
  * extract the next unit from the MinDistance order, allot it to its most
  * suitable center j (paying pen[j] if j had no vacancy), Negative Cycle
  * Refinement at j, and, if the allotment overloaded j, Negative Path
@@ -550,7 +551,7 @@ int oracle_asral(int64_t n, int64_t k, const int32_t *cm, const int32_t *cap,
  * zero cost, so a center holding p dummies has a 0-cost transfer edge to
  * every other center.  Units are visited in index order (the "unvisited"
  * reading of the loop condition); each replaces a dummy at the cheapest
- * center that still holds one (lowest index on ties), then Alg. 2 runs at
+ * center that still holds one (lowest index on ties), then Alg. 1 runs at
  * that center.  Dummy units sort after real units on equal transfer cost.
  * Outputs assign[n] over the extended center set (k means the dummy center)
  * and the extended objective (dummy center cost included).
@@ -606,7 +607,7 @@ int oracle_strict(int64_t n, int64_t k, const int32_t *cm, const int32_t *cap, i
                 if (0 < tc[idx]) { tc[idx] = 0; td[idx] = OR_DUMMY_UNIT; }
             }
         }
-        /* Def. 5 graph and Alg. 2 at anchor j */
+        /* Def. 9 graph and Alg. 1 at anchor j */
         for (int64_t i = 0; i < N * N; ++i) W[i] = OR_INF;
         for (int64_t u = 0; u < K; ++u) {
             for (int64_t v = 0; v < K; ++v) {

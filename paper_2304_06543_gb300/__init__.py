@@ -28,7 +28,7 @@ OK = 0
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_INVARIANT, ERR_STATE, ERR_NODEV, ERR_BUDGET = \
     -1, -2, -3, -4, -5, -6, -7, -8
 CM_I32, CM_I16 = 0, 1
-OPT_CLUSTER, OPT_NCYC_SKIP = 1, 2
+OPT_CLUSTER, OPT_NCYC_SKIP, OPT_NPATH_REUSE = 1, 2, 3
 TINF = 2**31 - 1
 
 _lib = None
@@ -43,10 +43,15 @@ class LbddError(RuntimeError):
         super().__init__(msg)
 
 
+_STAT_FIELDS = (
+    "rounds", "cycles_applied", "paths_applied", "bf_calls", "bf_sweeps", "bf_max_sweeps",
+    "moves", "ncyc_skipped", "rows_scanned", "cm_elem_bytes", "cluster_size",
+    "prologue_ns", "rounds_ns", "merge_ns", "relax_ns", "sync_ns", "gather_ns", "apply_ns",
+    "rescan_ns", "npath_reused", "col_rows", "front_sum")
+
+
 class _Stats(ctypes.Structure):
-    _fields_ = [(f, ctypes.c_int64) for f in (
-        "rounds", "cycles_applied", "paths_applied", "bf_calls", "bf_sweeps", "bf_max_sweeps",
-        "moves", "ncyc_skipped", "rows_scanned", "cm_elem_bytes", "cluster_size")]
+    _fields_ = [(f, ctypes.c_int64) for f in _STAT_FIELDS] + [("front_hist", ctypes.c_int64 * 6)]
 
 
 def load():
@@ -130,6 +135,18 @@ class Stats:
     rows_scanned: int
     cm_elem_bytes: int
     cluster_size: int
+    prologue_ns: int
+    rounds_ns: int
+    merge_ns: int
+    relax_ns: int
+    sync_ns: int
+    gather_ns: int
+    apply_ns: int
+    rescan_ns: int
+    npath_reused: int
+    col_rows: int
+    front_sum: int
+    front_hist: tuple
 
 
 def create(n, k, cm, cap, pen, stream=None, cm_dtype=None):
@@ -201,7 +218,9 @@ def loads(h, k: int):
 def get_stats(h) -> Stats:
     s = _Stats()
     _check(load().lbdd_get_stats(h, ctypes.byref(s)), "lbdd_get_stats")
-    return Stats(**{f: getattr(s, f) for f, _ in _Stats._fields_})
+    d = {f: getattr(s, f) for f in _STAT_FIELDS}
+    d["front_hist"] = tuple(s.front_hist)
+    return Stats(**d)
 
 
 def best_transfer_table(h, k: int):
@@ -244,7 +263,8 @@ def destroy(h):
 class Solver:
     """RAII wrapper around one lbdd_solver handle."""
 
-    def __init__(self, cm, cap, pen, stream=None, cluster: int = 0, ncyc_skip: bool = True):
+    def __init__(self, cm, cap, pen, stream=None, cluster: int = 0, ncyc_skip: bool = True,
+                 npath_reuse: bool = True):
         if isinstance(cm, np.ndarray):
             n, k = cm.shape
         else:
@@ -255,6 +275,8 @@ class Solver:
             set_option(self.h, OPT_CLUSTER, cluster)
         if not ncyc_skip:
             set_option(self.h, OPT_NCYC_SKIP, 0)
+        if not npath_reuse:
+            set_option(self.h, OPT_NPATH_REUSE, 0)
 
     def solve(self, max_rounds: int = -1):
         solve(self.h, max_rounds)

@@ -1,9 +1,9 @@
 // Persistent ASRAL solver: one thread-block cluster runs whole solves.
 //
 // Paper: Ramnath et al., "Load Balanced Demand Distribution under Overload
-// Penalties" (arXiv 2304.06543).  Alg. 1 (ASRAL main loop), Alg. 2 (Negative
-// Cycle Refinement), Alg. 3 (Negative Path Refinement, Appendix A), Defs. 4-6
-// (allotment subspace multigraph, NCyc and NPath graphs), Alg. 4 (parallel
+// Penalties" (arXiv 2304.06543).  Alg. 2 (ASRAL main loop), Alg. 1 (Negative
+// Cycle Refinement), Alg. 4 (Negative Path Refinement, Appendix A), Defs. 8-10
+// (allotment subspace multigraph, NCyc and NPath graphs), Alg. 3 (parallel
 // Bellman-Ford).
 //
 // GB300 design (not the paper's JCuda design, which copied the graph to the
@@ -11,10 +11,11 @@
 //  * the whole solve - prologue, all n rounds - runs inside one launch on one
 //    cluster of C CTAs; nothing returns to the host between rounds;
 //  * the best-transfer table T (the heap tops of the paper's BestTransHeaps)
-//    is a dense k x k table in global memory, column-partitioned: CTA r of the
-//    cluster owns columns [r*w, r*w + w) of every row and is the only CTA
-//    that reads or writes them, so Bellman-Ford relaxations, merges and
-//    segment rescans need no cross-CTA traffic for T;
+//    is a dense k x k table, column-partitioned: CTA r of the cluster owns
+//    columns [r*w, r*w + w) of every row and is the only CTA that reads or
+//    writes them.  The cost half of the owned slice also lives in the CTA's
+//    shared memory when it fits (int16 when CM is int16), so Bellman-Ford
+//    relaxations read shared memory; the unit half stays in global memory;
 //  * Bellman-Ford is the synchronous form with a frontier (only labels that
 //    changed in the previous sweep can improve a label); each sweep publishes
 //    the owned label changes in shared memory and the CTAs read each other's
@@ -24,12 +25,15 @@
 //    16-byte vector loads.
 // Tie-breaking is canonical and identical to the CPU oracle: (cost, unit)
 // lexicographic in T, lowest predecessor index on equal Bellman-Ford labels.
+#include <limits>
+
 #include "lbdd_device.cuh"
 
 namespace lbdd {
 
 struct Layout {
-  uint32_t dist, load, front, par, outv, outd, outctl, path, pathu, misc, red, total;
+  uint32_t dist, hop, load, cap, pen, front, par, outv, outd, inv, ind, incnt, insink, path, pathu,
+      misc, red, tsm, base_total, total;
 };
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -39,60 +43,99 @@ __host__ __device__ inline int32_t own_width(int32_t k, int32_t C, int32_t vpl) 
   return (w + vpl - 1) / vpl * vpl;
 }
 
+// Row stride of the shared cost slice: w plus padding that makes the stride
+// an odd number of 4-byte words, so lanes reading one column of different
+// rows hit different banks.
+__host__ __device__ inline int32_t slice_stride(int32_t w, int32_t elem) {
+  return w + (elem == 2 ? 2 : 1);
+}
+
 constexpr uint32_t kRedBytes = kThreads * 8 * 8;  // rescan partials, int16 CM
 
-__host__ __device__ inline Layout make_layout(int32_t k, int32_t C, int32_t vpl) {
+// Shared-memory carve-up; `base_total` excludes the cost slice, `total`
+// includes it (k x w entries of elem bytes).
+__host__ __device__ inline Layout make_layout(int32_t k, int32_t C, int32_t elem) {
   Layout L;
   uint32_t o = 0;
+  const int32_t vpl = 16 / elem;
   const uint32_t w = (uint32_t)own_width(k, C, vpl);
-  const uint32_t ku = (uint32_t)k;
+  const uint32_t ku = (uint32_t)k, Cu = (uint32_t)C;
   L.dist = o;   o = align16(o + 8u * ku);
+  L.hop = o;    o = align16(o + 4u * ku);
   L.load = o;   o = align16(o + 4u * ku);
+  L.cap = o;    o = align16(o + 4u * ku);
+  L.pen = o;    o = align16(o + 4u * ku);
   L.front = o;  o = align16(o + 4u * (ku + 1));
   L.par = o;    o = align16(o + 4u * w);
-  L.outv = o;   o = align16(o + 2u * 4u * w);
-  L.outd = o;   o = align16(o + 2u * 8u * w);
-  L.outctl = o; o = align16(o + 2u * 8u * 8u);
+  L.outv = o;   o = align16(o + 4u * w);              // this sweep's own changes
+  L.outd = o;   o = align16(o + 8u * w);
+  L.inv = o;    o = align16(o + 2u * Cu * w * 4u);     // inbox [2][C][w] nodes
+  L.ind = o;    o = align16(o + 2u * Cu * w * 8u);     // inbox [2][C][w] labels
+  L.incnt = o;  o = align16(o + 2u * Cu * 2u * 4u);    // inbox [2][C] {count, merge flag}
+  L.insink = o; o = align16(o + 2u * 4u * 8u);         // inbox [2] sink record
   L.path = o;   o = align16(o + 4u * (ku + 2));
   L.pathu = o;  o = align16(o + 4u * (ku + 2));
   L.misc = o;   o = align16(o + 8u * 16u);
   L.red = o;    o = align16(o + kRedBytes);
+  L.base_total = o;
+  L.tsm = o;    o = align16(o + (uint32_t)elem * ku * (uint32_t)slice_stride((int32_t)w, elem));
   L.total = o;
   return L;
 }
 
-// Slots of the per-buffer exchange control block.
-enum { OC_COUNT = 0, OC_SINK_CHANGED, OC_SINK_DIST, OC_SINK_PAR, OC_MERGE_CHANGED };
+// Sink record of an inbox buffer.
+enum { SK_CHANGED = 0, SK_DIST, SK_PAR };
 // Slots of the per-CTA scalar block.
-enum { MS_NFRONT = 0, MS_SINK_DIST, MS_SINK_PAR, MS_CNT, MS_FLAG, MS_TOTAL, MS_PATHLEN,
-       MS_ITEM, MS_SINK_CHG, MS_MERGE_ANY, MS_BAD };
+enum { MS_NFRONT = 0, MS_SINK_DIST, MS_SINK_PAR, MS_CNT, MS_TOTAL, MS_PATHLEN, MS_SINK_CHG,
+       MS_MERGE_ANY, MS_OWN_SINK_CHG, MS_OWN_SINK_DIST, MS_OWN_SINK_PAR, MS_NAFF };
+
+// Counters and timers kept by thread 0 of CTA 0 (shared memory, so that
+// they cost no registers in the other threads).
+struct Book {
+  int64_t delta, free_top, cycles, paths, bf_calls, bf_sweeps, bf_max, moves, skipped, rows;
+  int64_t t_merge, t_relax, t_sync, t_gather, t_apply, t_rescan;
+  int64_t npath_reused, col_rows, front_sum, front_hist[6];
+  int64_t err0;   // a guard tripped (corrupt state; never expected)
+};
 
 template <typename T>
 struct Solver {
-  static constexpr int VPL = 16 / (int)sizeof(T);
+  __device__ explicit Solver(const DevInst& inst) : I(inst) {}
 
-  DevInst I;
+  static constexpr int VPL = 16 / (int)sizeof(T);
+  using TS = T;                                           // cost type of the shared slice
+  static constexpr int32_t kTsInf = std::numeric_limits<TS>::max();
+
+  const DevInst& I;   // shared-memory copy of the current instance
   const T* cm;
-  int32_t n, k, C, rank, w, c0, c1, wr;
+  int32_t n, k, C, rank, w, ws, c0, c1, wr;
   int tid;
   int flags;
-  int64_t* s_dist;
+  bool tsm_on;        // owned cost slice resident in shared memory
+  int64_t* s_dist;    // label replica of every node
+  int32_t* s_hop;     // sweep of each node's last label change (replica)
   int32_t* s_load;
+  int32_t* s_cap;     // capacity replica
+  int32_t* s_pen;     // penalty replica
   int32_t* s_front;
-  int32_t* s_par;
-  int32_t* s_outv;    // [2][w]
-  int64_t* s_outd;    // [2][w]
-  int64_t* s_outctl;  // [2][8]
+  int32_t* s_par;     // parents of the owned columns
+  int32_t* s_outv;    // [w] owned columns improved in this sweep
+  int64_t* s_outd;    // [w] their new labels
+  int32_t* s_inv;     // inbox [2][C][w]: nodes changed by CTA r in a sweep
+  int64_t* s_ind;     // inbox [2][C][w]: their new labels
+  int32_t* s_incnt;   // inbox [2][C][2]: {count, merge flag} from CTA r
+  int64_t* s_insink;  // inbox [2][4]: sink record from the owner of column j
   int32_t* s_path;
   int32_t* s_pathu;
   int64_t* s_misc;
   unsigned char* s_red;
+  TS* s_tc;           // [k][ws] owned costs (if tsm_on)
   int buf;            // exchange buffer parity, advances every sweep
 
-  // rank-0 bookkeeping, valid in thread 0 of CTA 0 only
-  int64_t delta, free_top, cycles, paths, bf_calls, bf_sweeps, bf_max, moves, skipped, rows;
-  int64_t err0 = 0;   // CTA 0 thread 0: a guard tripped (corrupt state; never expected)
+  Book* B;            // CTA 0 thread 0 bookkeeping (shared memory)
+  int32_t pending_d = -1, pending_j = -1;
 
+  __device__ __forceinline__ bool timer() const { return rank == 0 && tid == 0; }
   __device__ __forceinline__ const T* row(int32_t d) const { return cm + (int64_t)d * I.ld; }
 
   __device__ __forceinline__ int32_t* mslot(int32_t c, int32_t idx) const {
@@ -100,13 +143,27 @@ struct Solver {
     return I.pool + ((int64_t)page << kPageShift) + (idx & (kPage - 1));
   }
 
+  // Owned cost of row u, owned column cl (kTInf for "no edge").
+  __device__ __forceinline__ int32_t own_cost(int32_t u, int cl) const {
+    if (tsm_on) {
+      const int32_t t = (int32_t)s_tc[u * ws + cl];
+      return t == kTsInf ? kTInf : t;
+    }
+    return I.tc[(int64_t)u * k + c0 + cl];
+  }
+  __device__ __forceinline__ void set_entry(int32_t u, int cl, int32_t t, int32_t d) {
+    I.tc[(int64_t)u * k + c0 + cl] = t;
+    I.td[(int64_t)u * k + c0 + cl] = d;
+    if (tsm_on) s_tc[u * ws + cl] = (TS)(t == kTInf ? kTsInf : t);
+  }
+
   // Member-list primitives, called by one thread of CTA 0 only.
   __device__ void list_append(int32_t c, int32_t d) {
     int32_t idx = I.seg_size[c];
-    if (c < 0 || c >= k || d < 0 || d >= n || idx < 0 || idx >= n) { err0 = ST_ERR_INVARIANT; return; }
+    if (c < 0 || c >= k || d < 0 || d >= n || idx < 0 || idx >= n) { B->err0 = ST_ERR_INVARIANT; return; }
     if ((idx & (kPage - 1)) == 0) {
-      if (free_top <= 0) { err0 = ST_ERR_INVARIANT; return; }
-      int32_t page = I.free_stack[--free_top];
+      if (B->free_top <= 0) { B->err0 = ST_ERR_INVARIANT; return; }
+      int32_t page = I.free_stack[--B->free_top];
       I.page_tab[(int64_t)c * I.max_pages + (idx >> kPageShift)] = page;
     }
     *mslot(c, idx) = d;
@@ -117,8 +174,8 @@ struct Solver {
   // any move of this path was applied).
   __device__ void list_remove_at(int32_t c, int32_t idx) {
     int32_t last = I.seg_size[c] - 1;
-    if (c < 0 || c >= k || idx < 0 || idx > last || free_top >= I.npages) {
-      err0 = ST_ERR_INVARIANT;
+    if (c < 0 || c >= k || idx < 0 || idx > last || B->free_top >= I.npages) {
+      B->err0 = ST_ERR_INVARIANT;
       return;
     }
     if (idx != last) {
@@ -127,12 +184,12 @@ struct Solver {
       I.pos[moved] = idx;
     }
     if ((last & (kPage - 1)) == 0)
-      I.free_stack[free_top++] = I.page_tab[(int64_t)c * I.max_pages + (last >> kPageShift)];
+      I.free_stack[B->free_top++] = I.page_tab[(int64_t)c * I.max_pages + (last >> kPageShift)];
     I.seg_size[c] = last;
   }
 
   // ------------------------------------------------------------ prologue --
-  // Alg. 1 line 1: s_min(d) = lowest-index minimum of CM row d; the
+  // Alg. 2, first step: s_min(d) = lowest-index minimum of CM row d; the
   // MinDistance heap's extraction order = stable sort of d by CM(d, s_min).
   __device__ void prologue() {
     const int lane = tid & 31, warp = tid >> 5;
@@ -201,7 +258,7 @@ struct Solver {
       int32_t *dk = (p & 1) ? k0 : k1, *dv = (p & 1) ? v0 : v1;
       for (int i = tid; i < 256; i += kThreads) s_off[i] = 0;
       __syncthreads();
-      for (int64_t i = tid; i < n; i += kThreads) atomicAdd(&s_off[(sk[i] >> shift) & 255], 1);
+      for (int64_t i = tid; i < n; i += kThreads) atomicAdd(&s_off[(__ldcg(sk + i) >> shift) & 255], 1);
       __syncthreads();
       if (tid == 0) {
         int32_t run = 0;
@@ -211,7 +268,7 @@ struct Solver {
       for (int64_t base = 0; base < n; base += kThreads) {
         const int64_t i = base + tid;
         const bool valid = i < n;
-        const int32_t key = valid ? sk[i] : 0, val = valid ? sv[i] : 0;
+        const int32_t key = valid ? __ldcg(sk + i) : 0, val = valid ? __ldcg(sv + i) : 0;
         const int dig = valid ? ((key >> shift) & 255) : 256;
         const uint32_t peers = __match_any_sync(0xffffffffu, dig);
         const int rk = __popc(peers & lt);
@@ -243,29 +300,41 @@ struct Solver {
     __syncthreads();
   }
 
+  // Owned cost slice from the global table (after a prologue or on resume).
+  __device__ void load_slice() {
+    if (!tsm_on) return;
+    for (int64_t u = 0; u < k; ++u)
+      for (int cl = tid; cl < w; cl += kThreads) {
+        const int32_t t = cl < wr ? __ldcg(I.tc + u * k + c0 + cl) : kTInf;
+        s_tc[u * ws + cl] = (TS)(t == kTInf ? kTsInf : t);
+      }
+    __syncthreads();
+  }
+
   // ---------------------------------------------------- best-transfer T --
-  // Alg. 1 line 6: unit d joins center j; its k-1 transfer edges
-  // CM(d, v) - CM(d, j) (Def. 4) enter the per-pair minima of row j.
-  // Returns (cluster-uniformly later) whether a cost of row j decreased.
+  // Alg. 2, allotment step: unit d joins center j; its k-1 transfer edges
+  // CM(d, v) - CM(d, j) (Def. 8) enter the per-pair minima of row j.
+  // Returns whether a cost of row j decreased in this CTA's columns.
   __device__ bool merge_row(int32_t d, int32_t j) {
     bool changed = false;
     const int S = w / VPL;
     if (tid < S) {
       const T* r = row(d);
       const int32_t own = (int32_t)r[j];
-      const int col = c0 + tid * VPL;
-      Vec16<T> x = load16(r + col);
+      const int cl0 = tid * VPL;
+      Vec16<T> x = load16(r + c0 + cl0);
 #pragma unroll
       for (int q = 0; q < VPL; ++q) {
-        const int v = col + q;
+        const int cl = cl0 + q, v = c0 + cl;
         if (v < k && v != j) {
           const int32_t t = (int32_t)x.v[q] - own;
-          const int64_t idx = (int64_t)j * k + v;
-          const int32_t bt = I.tc[idx], bd = I.td[idx];
-          if (lex_less(t, d, bt, bd)) {
-            I.tc[idx] = t;
-            I.td[idx] = d;
-            changed |= (t < bt);
+          const int32_t bt = own_cost(j, cl);
+          if (t <= bt) {
+            const int32_t bd = I.td[(int64_t)j * k + v];
+            if (lex_less(t, d, bt, bd)) {
+              set_entry(j, cl, t, d);
+              changed |= (t < bt);
+            }
           }
         }
       }
@@ -276,6 +345,7 @@ struct Solver {
   // Row c of T over the owned columns, recomputed from c's member list:
   // T[c][v] = lexmin over d in seg(c) of (CM(d, v) - CM(d, c), d).
   __device__ void rescan(int32_t c) {
+    constexpr int U = 4;   // member rows in flight per thread
     const int S = w / VPL;
     const int R = kThreads / S;
     const int slot = tid % S, g = tid / S;
@@ -285,16 +355,32 @@ struct Solver {
 #pragma unroll
     for (int q = 0; q < VPL; ++q) { bt[q] = kTInf; bd[q] = -1; }
     if (g < R) {
-      for (int32_t idx = g; idx < s; idx += R) {
-        const int32_t d = __ldcg(mslot(c, idx));
-        if ((uint32_t)d >= (uint32_t)n) continue;   // guard: corrupt list entry
-        const T* r = row(d);
-        const int32_t own = (int32_t)r[c];
-        Vec16<T> x = load16(r + c0 + slot * VPL);
+      for (int32_t base = g; base < s; base += U * R) {
+        int32_t dd[U];
 #pragma unroll
-        for (int q = 0; q < VPL; ++q) {
-          const int32_t t = (int32_t)x.v[q] - own;
-          if (lex_less(t, d, bt[q], bd[q])) { bt[q] = t; bd[q] = d; }
+        for (int u = 0; u < U; ++u) {
+          const int32_t idx = base + u * R;
+          dd[u] = idx < s ? __ldcg(mslot(c, idx)) : -1;
+          if ((uint32_t)dd[u] >= (uint32_t)n) dd[u] = -1;   // guard: corrupt entry
+        }
+        int32_t own[U];
+        Vec16<T> x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (dd[u] >= 0) {
+            const T* r = row(dd[u]);
+            own[u] = (int32_t)r[c];
+            x[u] = load16(r + c0 + slot * VPL);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (dd[u] < 0) continue;
+#pragma unroll
+          for (int q = 0; q < VPL; ++q) {
+            const int32_t t = (int32_t)x[u].v[q] - own[u];
+            if (lex_less(t, dd[u], bt[q], bd[q])) { bt[q] = t; bd[q] = dd[u]; }
+          }
         }
       }
     }
@@ -304,155 +390,204 @@ struct Solver {
       for (int q = 0; q < VPL; ++q) red[g * w + slot * VPL + q] = make_int2(bt[q], bd[q]);
     }
     __syncthreads();
-    for (int col = tid; col < w; col += kThreads) {
-      const int v = c0 + col;
-      if (v >= k) continue;
+    for (int cl = tid; cl < wr; cl += kThreads) {
+      const int v = c0 + cl;
       int32_t t = kTInf, d = -1;
       for (int gg = 0; gg < R; ++gg) {
-        int2 e = red[gg * w + col];
+        int2 e = red[gg * w + cl];
         if (lex_less(e.x, e.y, t, d)) { t = e.x; d = e.y; }
       }
       if (v == c) { t = kTInf; d = -1; }
-      I.tc[(int64_t)c * k + v] = t;
-      I.td[(int64_t)c * k + v] = d;
+      set_entry(c, cl, t, d);
     }
-    if (rank == 0 && tid == 0) rows += s;
+    if (rank == 0 && tid == 0) B->rows += s;
     __syncthreads();
   }
 
   // -------------------------------------------------------- Bellman-Ford --
   // Lexicographic minimum of (label[u] + weight(u, v), u) over this
-  // thread's share of the frontier (entries fg, fg+FG, ...).
-  __device__ __forceinline__ void relax_column(int v, bool valid, int fg, int FG, int nfront,
-                                               int32_t j, bool npath, int32_t pen_j,
-                                               int64_t& bc, int32_t& bu) const {
+  // lane's share of the frontier (entries g, g+G, ...).
+  // Lexicographic minimum of (label[u] + weight(u, v), u) over the frontier
+  // entries slice, slice+step, ...  Lanes of a warp hold consecutive owned
+  // columns and walk the same frontier entries, so the label read is a
+  // broadcast and the cost reads are consecutive (no bank conflicts).
+  __device__ __forceinline__ void relax_column(int cl, bool valid, int slice, int step,
+                                               int nfront, int32_t j, bool npath,
+                                               int32_t pen_j, int64_t& bc, int32_t& bu) const {
     bc = kDInf;
     bu = INT32_MAX;
-    if (!valid) return;
-    for (int f = fg; f < nfront; f += FG) {
-      const int32_t u = s_front[f];
-      int64_t wgt;
-      if (v == j) {                    // edge u -> s*in
-        if (u == j) continue;
-        if (npath) {
-          wgt = (int64_t)(s_load[u] >= I.cap[u] ? I.pen[u] : 0) - pen_j;
-        } else {
-          const int32_t t = I.tc[(int64_t)u * k + j];
-          if (t == kTInf) continue;
-          wgt = t;
-        }
-      } else {                         // transfer edge u -> v
-        const int32_t t = I.tc[(int64_t)u * k + v];
-        if (t == kTInf) continue;
-        wgt = t;
+    const int v = c0 + cl;
+    const bool pen_edge = valid && (v == j) && npath;
+    constexpr int U = 4;
+    int f = slice;
+    for (; f + (U - 1) * step < nfront; f += U * step) {
+      int32_t u[U], t[U];
+      int64_t du[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) u[q] = s_front[f + q * step];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        du[q] = s_dist[u[q]];
+        if (pen_edge)                 // Def. 10 (c): q_u() - q_{s*}()
+          t[q] = (u[q] == j) ? kTInf : (s_load[u[q]] >= s_cap[u[q]] ? s_pen[u[q]] : 0) - pen_j;
+        else                          // transfer edge u -> v (v == j: into s*in)
+          t[q] = valid ? own_cost(u[q], cl) : kTInf;
       }
-      const int64_t c = s_dist[u] + wgt;
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        if (t[q] == kTInf) continue;
+        const int64_t c = du[q] + t[q];
+        if (c < bc || (c == bc && u[q] < bu)) { bc = c; bu = u[q]; }
+      }
+    }
+    for (; f < nfront; f += step) {
+      const int32_t u = s_front[f];
+      int32_t t;
+      if (pen_edge) t = (u == j) ? kTInf : (s_load[u] >= s_cap[u] ? s_pen[u] : 0) - pen_j;
+      else t = valid ? own_cost(u, cl) : kTInf;
+      if (t == kTInf) continue;
+      const int64_t c = s_dist[u] + t;
       if (c < bc || (c == bc && u < bu)) { bc = c; bu = u; }
     }
   }
 
-  // Strict improvement of owned column cl: publish it for the gather.
-  __device__ __forceinline__ void record_change(int cl, int64_t bc, int32_t bu, int32_t j,
-                                                int64_t sink_dist, int32_t* outv,
-                                                int64_t* outd, int64_t* oc) {
+  // Strict improvement of owned column cl: record it in the local out list
+  // (pushed to every CTA after the relaxation) or as the sink's new label.
+  __device__ __forceinline__ void record(int cl, int64_t bc, int32_t bu, int32_t j,
+                                         int64_t sink_dist) {
     const int v = c0 + cl;
     const int64_t cur = (v == j) ? sink_dist : s_dist[v];
     if (bc < cur) {
       if (v == j) {
-        oc[OC_SINK_CHANGED] = 1;
-        oc[OC_SINK_DIST] = bc;
-        oc[OC_SINK_PAR] = bu;
+        s_misc[MS_OWN_SINK_CHG] = 1;
+        s_misc[MS_OWN_SINK_DIST] = bc;
+        s_misc[MS_OWN_SINK_PAR] = bu;
       } else {
         const int at = atomicAdd(reinterpret_cast<int*>(&s_misc[MS_CNT]), 1);
-        outv[at] = v;
-        outd[at] = bc;
+        s_outv[at] = v;
+        s_outd[at] = bc;
         s_par[cl] = bu;
       }
     }
   }
 
-
-  // Canonical synchronous Bellman-Ford from the anchor j (Alg. 4 / Sections
+  // Canonical synchronous Bellman-Ford from the anchor j (Alg. 3 / Sections
   // 3.3-3.4).  Node u < k is center u, node j is s*out (the source) and the
   // sink s*in is represented by column j: an edge u -> s*in is
-  //   NCyc (Def. 5 (c)): the best transfer u -> j,
-  //   NPath (Def. 6 (c)): q_u() - q_j(), q_u() = pen[u] if load[u] >= cap[u].
+  //   NCyc (Def. 9 (c)): the best transfer u -> j,
+  //   NPath (Def. 10 (c)): q_u() - q_j(), q_u() = pen[u] if load[u] >= cap[u].
   // No edge enters the source.  Labels change only on strict improvement and
   // take the lowest-index predecessor among equal candidates.
+  //
+  // Exchange: the owner of a column that improves stores (node, label) into
+  // an inbox of every CTA of the cluster before the sweep's barrier; after
+  // the barrier each CTA applies its local inbox, so the only cross-CTA
+  // operations are remote stores.  Inboxes are double-buffered by sweep
+  // parity: buffer b is rewritten two barriers after it was read.
   // Returns 1 for a negative sink label (path to apply), 0 for none, and
   // < 0 on a broken invariant.  `merged` says whether this CTA's merge of
   // the round's unit lowered a cost of row j (NegCycle only).
   __device__ int bellman_ford(int32_t j, bool npath, bool merged, bool allow_skip) {
-    for (int v = tid; v < k; v += kThreads) s_dist[v] = (v == j) ? 0 : kDInf;
+    for (int v = tid; v < k; v += kThreads) {
+      s_dist[v] = (v == j) ? 0 : kDInf;
+      s_hop[v] = (v == j) ? 0 : -1;
+    }
     for (int v = tid; v < w; v += kThreads) s_par[v] = -1;
     if (tid == 0) {
       s_front[0] = j;
       s_misc[MS_NFRONT] = 1;
       s_misc[MS_SINK_DIST] = kDInf;
       s_misc[MS_SINK_PAR] = -1;
+      s_misc[MS_CNT] = 0;
     }
     __syncthreads();
     const int owner_j = j / w;
-    const int32_t pen_j = I.pen[j];
-    const int NTc = min(kThreads, max(32, (wr + 31) / 32 * 32));
-    const int FG = kThreads / NTc;
-    const int cl0 = tid % NTc, fg = tid / NTc;
+    const int32_t pen_j = __ldg(I.pen + j);
+    // lanes own 32 consecutive columns (a column block); the WPB warps of a
+    // block split the frontier and their minima are combined in shared memory
+    const int CB = max(1, (wr + 31) / 32);
+    const int WPB = max(1, kWarps / CB);
+    const int lane = tid & 31, warp = tid >> 5;
+    int* s_cntloc = reinterpret_cast<int*>(&s_misc[MS_CNT]);
+    int32_t* s_cnt = reinterpret_cast<int32_t*>(s_red);                   // [C+1] prefix
+    int64_t* red_c = reinterpret_cast<int64_t*>(s_red + 256);             // [WPB][CB*32]
+    int32_t* red_u = reinterpret_cast<int32_t*>(s_red + 256 + 8 * kThreads);
     int result = 0;
     for (int sweep = 1;; ++sweep) {
+      const uint64_t t0 = timer() ? clock_cycles() : 0;
       const int nfront = (int)s_misc[MS_NFRONT];
       const int64_t sink_dist = s_misc[MS_SINK_DIST];
-      if (tid == 0) s_misc[MS_CNT] = 0;
-      int32_t* outv = s_outv + buf * w;
-      int64_t* outd = s_outd + buf * w;
-      int64_t* oc = s_outctl + buf * 8;
-      if (tid == 0) { oc[OC_SINK_CHANGED] = 0; oc[OC_MERGE_CHANGED] = merged ? 1 : 0; }
+      if (timer()) {
+        B->front_sum += nfront;
+        B->front_hist[nfront <= 1 ? 0 : nfront <= 4 ? 1 : nfront <= 16 ? 2 : nfront <= 64 ? 3
+                      : nfront <= 256 ? 4 : 5]++;
+      }
+      int32_t* inv = s_inv + buf * C * w;
+      int64_t* ind = s_ind + buf * C * w;
+      int32_t* incnt = s_incnt + buf * C * 2;
+      int64_t* insink = s_insink + buf * 4;
+      if (tid == 0) s_misc[MS_OWN_SINK_CHG] = 0;
       __syncthreads();
       // relax all edges out of the frontier into the owned columns
-      int64_t* red_c = reinterpret_cast<int64_t*>(s_red);
-      int32_t* red_u = reinterpret_cast<int32_t*>(s_red + 8 * kThreads);
-      const bool active = fg < FG;
-      if (FG > 1) {
-        // one owned column per thread, frontier split over FG groups
-        if (active) {
-          int64_t bc; int32_t bu;
-          relax_column(c0 + cl0, cl0 < wr, fg, FG, nfront, j, npath, pen_j, bc, bu);
-          red_c[fg * NTc + cl0] = bc;
-          red_u[fg * NTc + cl0] = bu;
+      if (WPB > 1) {
+        const int blk = warp / WPB, slice = warp % WPB;
+        if (blk < CB) {
+          const int cl = blk * 32 + lane;
+          int64_t bc;
+          int32_t bu;
+          relax_column(cl, cl < wr, slice, WPB, nfront, j, npath, pen_j, bc, bu);
+          red_c[slice * CB * 32 + cl] = bc;
+          red_u[slice * CB * 32 + cl] = bu;
         }
         __syncthreads();
-        if (fg == 0 && cl0 < wr) {
+        for (int cl = tid; cl < wr; cl += kThreads) {
           int64_t bc = kDInf;
           int32_t bu = INT32_MAX;
-          for (int g2 = 0; g2 < FG; ++g2) {
-            const int64_t c = red_c[g2 * NTc + cl0];
-            const int32_t u = red_u[g2 * NTc + cl0];
+          for (int sl = 0; sl < WPB; ++sl) {
+            const int64_t c = red_c[sl * CB * 32 + cl];
+            const int32_t u = red_u[sl * CB * 32 + cl];
             if (c < bc || (c == bc && u < bu)) { bc = c; bu = u; }
           }
-          record_change(cl0, bc, bu, j, sink_dist, outv, outd, oc);
+          record(cl, bc, bu, j, sink_dist);
         }
-      } else if (active) {
-        for (int cl = cl0; cl < wr; cl += NTc) {
-          int64_t bc; int32_t bu;
-          relax_column(c0 + cl, true, 0, 1, nfront, j, npath, pen_j, bc, bu);
-          record_change(cl, bc, bu, j, sink_dist, outv, outd, oc);
+      } else {
+        for (int blk = warp; blk < CB; blk += kWarps) {
+          const int cl = blk * 32 + lane;
+          int64_t bc;
+          int32_t bu;
+          relax_column(cl, cl < wr, 0, 1, nfront, j, npath, pen_j, bc, bu);
+          if (cl < wr) record(cl, bc, bu, j, sink_dist);
         }
       }
       __syncthreads();
-      if (tid == 0) oc[OC_COUNT] = (int32_t)s_misc[MS_CNT];
-      __syncthreads();
-      cluster_sync_all();
-      commit_pending();
-      // gather every CTA's changes (same order in every CTA)
-      int32_t* s_cnt = reinterpret_cast<int32_t*>(s_red + 12 * kThreads);   // [C+1] prefix
-      if (tid < 32) {
-        // lane r reads CTA r's counters; a warp scan forms the offsets
-        const int lane = tid;
-        int32_t cnt = 0;
-        int64_t mg = 0;
-        if (lane < C) {
-          cnt = (int32_t)dsmem_ld64(dsmem_addr(s_outctl + buf * 8 + OC_COUNT, lane));
-          mg = dsmem_ld64(dsmem_addr(s_outctl + buf * 8 + OC_MERGE_CHANGED, lane));
+      // push this CTA's changes into every CTA's inbox (all threads help)
+      {
+        const int cnt = *s_cntloc;
+        for (int i = tid; i < cnt * C; i += kThreads) {
+          const int e = i / C, r = i - e * C;
+          dsmem_st32(dsmem_addr(inv + rank * w + e, r), s_outv[e]);
+          dsmem_st64(dsmem_addr(ind + rank * w + e, r), s_outd[e]);
         }
+        if (tid >= kThreads - 32 && tid - (kThreads - 32) < C) {
+          const uint32_t r = tid - (kThreads - 32);
+          dsmem_st32(dsmem_addr(incnt + rank * 2, r), cnt);
+          dsmem_st32(dsmem_addr(incnt + rank * 2 + 1, r), merged ? 1 : 0);
+        }
+        if (rank == owner_j && tid >= kThreads - 64 && tid - (kThreads - 64) < C) {
+          const uint32_t r = tid - (kThreads - 64);
+          dsmem_st64(dsmem_addr(insink + SK_CHANGED, r), s_misc[MS_OWN_SINK_CHG]);
+          dsmem_st64(dsmem_addr(insink + SK_DIST, r), s_misc[MS_OWN_SINK_DIST]);
+          dsmem_st64(dsmem_addr(insink + SK_PAR, r), s_misc[MS_OWN_SINK_PAR]);
+        }
+      }
+      const uint64_t t1 = timer() ? clock_cycles() : 0;
+      cluster_sync_all();
+      const uint64_t t2 = timer() ? clock_cycles() : 0;
+      commit_pending();
+      // apply the local inbox (same order in every CTA)
+      if (tid < 32) {
+        int32_t cnt = 0, mg = 0;
+        if (lane < C) { cnt = incnt[lane * 2]; mg = incnt[lane * 2 + 1]; }
         int32_t inc = cnt;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -464,14 +599,11 @@ struct Solver {
         if (lane == C - 1) { s_cnt[C] = inc; s_misc[MS_TOTAL] = inc; }
         if (lane == 0) {
           s_misc[MS_MERGE_ANY] = any ? 1 : 0;
-          const int64_t chg =
-              dsmem_ld64(dsmem_addr(s_outctl + buf * 8 + OC_SINK_CHANGED, owner_j));
+          const int64_t chg = insink[SK_CHANGED];
           s_misc[MS_SINK_CHG] = chg;
           if (chg) {
-            s_misc[MS_SINK_DIST] =
-                dsmem_ld64(dsmem_addr(s_outctl + buf * 8 + OC_SINK_DIST, owner_j));
-            s_misc[MS_SINK_PAR] =
-                dsmem_ld64(dsmem_addr(s_outctl + buf * 8 + OC_SINK_PAR, owner_j));
+            s_misc[MS_SINK_DIST] = insink[SK_DIST];
+            s_misc[MS_SINK_PAR] = insink[SK_PAR];
           }
         }
       }
@@ -481,26 +613,35 @@ struct Solver {
         int r = 0;
         while (s_cnt[r + 1] <= i) ++r;
         const int li = i - s_cnt[r];
-        const int32_t v = dsmem_ld32(dsmem_addr(s_outv + buf * w + li, r));
-        const int64_t dd = dsmem_ld64(dsmem_addr(s_outd + buf * w + li, r));
+        const int32_t v = inv[r * w + li];
         s_front[i] = v;
-        s_dist[v] = dd;
+        s_dist[v] = ind[r * w + li];
+        s_hop[v] = sweep;
       }
-      if (tid == 0) s_misc[MS_NFRONT] = total;
+      if (tid == 0) {
+        s_misc[MS_NFRONT] = total;
+        s_misc[MS_CNT] = 0;
+      }
       __syncthreads();
+      if (timer()) {
+        const uint64_t t3 = clock_cycles();
+        B->t_relax += t1 - t0;
+        B->t_sync += t2 - t1;
+        B->t_gather += t3 - t2;
+      }
       buf ^= 1;
       const bool sink_chg = s_misc[MS_SINK_CHG] != 0;
       if (sweep == 1 && allow_skip && s_misc[MS_MERGE_ANY] == 0) {
         // T is unchanged since the last round, whose Gamma had no negative
         // cycle (Lemmas 1/2): the NegCycle sink label cannot be negative.
-        if (rank == 0 && tid == 0) skipped++;
+        if (rank == 0 && tid == 0) B->skipped++;
         return 0;
       }
       if (total == 0 && !sink_chg) {
         if (rank == 0 && tid == 0) {
-          bf_calls++;
-          bf_sweeps += sweep;
-          bf_max = max(bf_max, (int64_t)sweep);
+          B->bf_calls++;
+          B->bf_sweeps += sweep;
+          B->bf_max = max(B->bf_max, (int64_t)sweep);
         }
         result = s_misc[MS_SINK_DIST] < 0 ? 1 : 0;
         break;
@@ -508,6 +649,49 @@ struct Solver {
       if (sweep >= k + 1) { result = -1; break; }
     }
     return result;
+  }
+
+  // Alg. 4 right after an Alg. 1 that applied nothing: T and the loads are
+  // unchanged, and the NPath graph differs from the NCyc graph only in the
+  // edges into the sink, which have no successors.  The converged node
+  // labels are therefore already the NPath labels, and the sink's label and
+  // parent follow from one reduction: the synchronous sweep reaches the
+  // minimum first through the predecessors u of smallest hop count (the
+  // sweep of u's last change), and among those takes the lowest index.
+  // Every CTA computes the same result from its replicas.  Returns 1 if the
+  // sink label is negative.
+  __device__ int npath_from_ncyc(int32_t j) {
+    const int32_t pen_j = __ldg(I.pen + j);
+    int64_t bc = kDInf;
+    int32_t bh = INT32_MAX, bu = INT32_MAX;
+    for (int u = tid; u < k; u += kThreads) {
+      if (u == j || s_dist[u] >= kDInf) continue;
+      const int64_t c = s_dist[u] + (int64_t)(s_load[u] >= s_cap[u] ? s_pen[u] : 0) - pen_j;
+      const int32_t h = s_hop[u];
+      if (c < bc || (c == bc && (h < bh || (h == bh && u < bu)))) { bc = c; bh = h; bu = u; }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const int64_t oc = __shfl_xor_sync(0xffffffffu, bc, off);
+      const int32_t oh = __shfl_xor_sync(0xffffffffu, bh, off);
+      const int32_t ou = __shfl_xor_sync(0xffffffffu, bu, off);
+      if (oc < bc || (oc == bc && (oh < bh || (oh == bh && ou < bu)))) { bc = oc; bh = oh; bu = ou; }
+    }
+    int64_t* rc = reinterpret_cast<int64_t*>(s_red);
+    int32_t* rh = reinterpret_cast<int32_t*>(s_red + 8 * kWarps);
+    int32_t* ru = rh + kWarps;
+    if ((tid & 31) == 0) { rc[tid >> 5] = bc; rh[tid >> 5] = bh; ru[tid >> 5] = bu; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int i = 1; i < kWarps; ++i)
+        if (rc[i] < bc || (rc[i] == bc && (rh[i] < bh || (rh[i] == bh && ru[i] < bu)))) {
+          bc = rc[i]; bh = rh[i]; bu = ru[i];
+        }
+      s_misc[MS_SINK_DIST] = bc;
+      s_misc[MS_SINK_PAR] = bc < kDInf ? bu : -1;
+      if (rank == 0) B->npath_reused++;
+    }
+    __syncthreads();
+    return s_misc[MS_SINK_DIST] < 0 ? 1 : 0;
   }
 
   // Follow parents from the sink back to the anchor (every CTA does this,
@@ -532,22 +716,28 @@ struct Solver {
     return (int)s_misc[MS_PATHLEN];
   }
 
-  // Apply the transfers of the path (Alg. 2 lines 5-9, Alg. 3 lines 5-10);
+  // Apply the transfers of the path (Alg. 1 and Alg. 4, "if cost < 0" branch);
   // then recompute the rows of T of every center on it.  For NCyc every
   // center on the cycle loses one unit and gains one; for NPath the anchor
   // only loses one and the terminal center only gains one.
   __device__ void apply(int32_t j, bool npath, int m) {
-    if (rank == 0 && tid < 32) {
-      const int lane = tid;
-      int32_t* ppos = reinterpret_cast<int32_t*>(s_red);   // positions of the outgoing units
-      for (int i = lane; i < m; i += 32) {
+    uint64_t t0 = timer() ? clock_cycles() : 0;
+    if (tid < 32) {
+      // every CTA reads the moved units (T is not written before the
+      // barrier below, so all CTAs see the same entries)
+      for (int i = tid; i < m; i += 32) {
         const int32_t from = s_path[i];
         const int32_t to = (i + 1 < m) ? s_path[i + 1] : (npath ? -1 : j);
         int32_t x = to >= 0 ? __ldcg(I.td + (int64_t)from * k + to) : -1;
-        if (to >= 0 && (uint32_t)x >= (uint32_t)n) { x = -1; err0 = ST_ERR_INVARIANT; }
+        if (to >= 0 && (uint32_t)x >= (uint32_t)n) { x = -1; if (rank == 0) B->err0 = ST_ERR_INVARIANT; }
         s_pathu[i] = x;
-        ppos[i] = x >= 0 ? I.pos[x] : -1;
       }
+      __syncwarp();
+    }
+    if (rank == 0 && tid < 32) {
+      const int lane = tid;
+      int32_t* ppos = reinterpret_cast<int32_t*>(s_red);   // positions of the outgoing units
+      for (int i = lane; i < m; i += 32) ppos[i] = s_pathu[i] >= 0 ? I.pos[s_pathu[i]] : -1;
       __syncwarp();
       // in-place replacements: center p_i swaps its leaving unit for the
       // arriving unit x_{i-1} (cyclically for NCyc)
@@ -567,16 +757,16 @@ struct Solver {
           // the anchor loses x_0, the terminal center gains x_{m-2}
           list_remove_at(j, ppos[0]);
           if (s_pathu[m - 2] >= 0) list_append(s_path[m - 1], s_pathu[m - 2]);
-          else err0 = ST_ERR_INVARIANT;
+          else B->err0 = ST_ERR_INVARIANT;
           I.load[j] -= 1;
           I.load[s_path[m - 1]] += 1;
-          paths++;
-          moves += m - 1;
+          B->paths++;
+          B->moves += m - 1;
         } else {
-          cycles++;
-          moves += m;
+          B->cycles++;
+          B->moves += m;
         }
-        delta += s_misc[MS_SINK_DIST];
+        B->delta += s_misc[MS_SINK_DIST];
       }
     }
     if (npath && tid == 0) {   // load replicas in every CTA
@@ -585,51 +775,151 @@ struct Solver {
     }
     __syncthreads();
     cluster_sync_all();   // member lists updated before anyone rescans
-    for (int i = 0; i < m; ++i) rescan(s_path[i]);
+    uint64_t t1 = timer() ? clock_cycles() : 0;
+    for (int i = 0; i < m; ++i) {
+      const int32_t x_out = s_pathu[i];
+      const int32_t x_in = (i > 0) ? s_pathu[i - 1] : (npath ? -1 : s_pathu[m - 1]);
+      rescan_incremental(s_path[i], x_out, x_in);
+    }
+    if (timer()) {
+      const uint64_t t2 = clock_cycles();
+      B->t_apply += t1 - t0;
+      B->t_rescan += t2 - t1;
+    }
+  }
+
+  // Row c of T after c lost unit x_out and gained unit x_in (either may be
+  // -1), equal to a full rescan of c's new member list:
+  //  * columns whose best unit was not x_out keep their minimum over the
+  //    remaining members, so only x_in is merged in;
+  //  * columns whose best unit was x_out are recomputed over all members;
+  //    with many such columns the whole owned row is rescanned instead.
+  __device__ void rescan_incremental(int32_t c, int32_t x_out, int32_t x_in) {
+    int32_t* s_aff = reinterpret_cast<int32_t*>(s_red);                       // [w]
+    unsigned long long* s_best =
+        reinterpret_cast<unsigned long long*>(s_red + 4 * ((w + 1) & ~1));   // [naff]
+    if (tid == 0) s_misc[MS_NAFF] = 0;
+    __syncthreads();
+    int32_t in_own = 0;
+    const T* rin = nullptr;
+    if (x_in >= 0) { rin = row(x_in); in_own = (int32_t)rin[c]; }
+    for (int cl = tid; cl < wr; cl += kThreads) {
+      const int v = c0 + cl;
+      if (v == c) continue;
+      const int32_t bd = I.td[(int64_t)c * k + v];
+      if (x_out >= 0 && bd == x_out) {
+        s_aff[atomicAdd(reinterpret_cast<int*>(&s_misc[MS_NAFF]), 1)] = cl;
+      } else if (x_in >= 0) {
+        const int32_t t = (int32_t)rin[v] - in_own;
+        const int32_t bt = own_cost(c, cl);
+        if (lex_less(t, x_in, bt, bd)) set_entry(c, cl, t, x_in);
+      }
+    }
+    __syncthreads();
+    const int naff = (int)s_misc[MS_NAFF];
+    if (naff == 0) return;
+    if (naff * 4 > wr) { rescan(c); return; }
+    for (int a = tid; a < naff; a += kThreads) s_best[a] = ~0ull;
+    __syncthreads();
+    const int32_t s = __ldcg(I.seg_size + c);
+    const int stride = kThreads / naff;
+    const int a = tid % naff, i0 = tid / naff;
+    if (i0 < stride) {
+      const int v = c0 + s_aff[a];
+      unsigned long long best = ~0ull;
+      constexpr int U = 4;
+      for (int32_t base = i0; base < s; base += U * stride) {
+        int32_t dd[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int32_t idx = base + u * stride;
+          dd[u] = idx < s ? __ldcg(mslot(c, idx)) : -1;
+          if ((uint32_t)dd[u] >= (uint32_t)n) dd[u] = -1;   // guard: corrupt entry
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (dd[u] < 0) continue;
+          const T* r = row(dd[u]);
+          const int32_t t = (int32_t)r[v] - (int32_t)r[c];
+          const unsigned long long key =
+              ((unsigned long long)(uint32_t)(t + (int64_t)2147483648LL) << 32) | (uint32_t)dd[u];
+          best = min(best, key);
+        }
+      }
+      if (best != ~0ull) atomicMin(&s_best[a], best);
+    }
+    __syncthreads();
+    for (int b = tid; b < naff; b += kThreads) {
+      const unsigned long long e = s_best[b];
+      if (e == ~0ull) set_entry(c, s_aff[b], kTInf, -1);
+      else set_entry(c, s_aff[b], (int32_t)((int64_t)(e >> 32) - 2147483648LL), (int32_t)(e & 0xffffffffu));
+    }
+    if (rank == 0 && tid == 0) B->col_rows += s;
+    __syncthreads();
   }
 
   // ---------------------------------------------------------- the loop --
   __device__ void run_rounds() {
+    const uint64_t tstart = timer() ? gtimer_ns() : 0;
+    const uint64_t cstart = timer() ? clock_cycles() : 0;
     const int64_t r_begin = I.ctl[CTL_ROUNDS];
     const int64_t r_end = min((int64_t)n, I.ctl[CTL_TARGET]);
-    for (int v = tid; v < k; v += kThreads) s_load[v] = __ldcg(I.load + v);
-    if (rank == 0 && tid == 0) {
-      delta = I.ctl[CTL_DELTA];
-      free_top = I.ctl[CTL_FREE_TOP];
-      cycles = paths = bf_calls = bf_sweeps = bf_max = moves = skipped = rows = 0;
+    for (int v = tid; v < k; v += kThreads) {
+      s_load[v] = __ldcg(I.load + v);
+      s_cap[v] = __ldg(I.cap + v);
+      s_pen[v] = __ldg(I.pen + v);
     }
+    if (rank == 0 && tid == 0) {
+      B->delta = I.ctl[CTL_DELTA];
+      B->free_top = I.ctl[CTL_FREE_TOP];
+      B->cycles = B->paths = B->bf_calls = B->bf_sweeps = B->bf_max = B->moves = B->skipped = B->rows = 0;
+      B->t_merge = B->t_relax = B->t_sync = B->t_gather = B->t_apply = B->t_rescan = 0;
+      B->err0 = 0;
+      B->npath_reused = 0;
+      B->col_rows = 0;
+      B->front_sum = 0;
+      for (int h = 0; h < 6; ++h) B->front_hist[h] = 0;
+    }
+    load_slice();
     __syncthreads();
     const bool allow_skip = !(flags & OPT_NO_NCYC_SKIP);
     int64_t status = ST_OK;
     int64_t r = r_begin;
     for (; r < r_end; ++r) {
-      // Alg. 1 lines 5-6 and 9-13: next unit of the MinDistance order goes
+      // Alg. 2 (extract-min, allot, objective update): next unit of the MinDistance order goes
       // to its most suitable center; pay the penalty if it had no vacancy.
+      const uint64_t tm0 = timer() ? clock_cycles() : 0;
       const int32_t d = __ldcg(I.order + r);
       if ((uint32_t)d >= (uint32_t)n) { status = ST_ERR_INVARIANT; break; }   // uniform guard
       const int32_t j = __ldcg(I.smin + d);
       if ((uint32_t)j >= (uint32_t)k) { status = ST_ERR_INVARIANT; break; }
-      const bool over = s_load[j] >= I.cap[j];
+      const bool over = s_load[j] >= __ldg(I.cap + j);
       const bool merged = merge_row(d, j);
       if (tid == 0) s_load[j] += 1;
       if (rank == 0 && tid == 0) {
         // Member lists are touched only after the next cluster barrier (the
         // first Bellman-Ford sweep), when every CTA has finished reading
         // them for the previous round's rescans.
-        delta += (int64_t)row(d)[j] + (over ? (int64_t)I.pen[j] : 0);
+        B->delta += (int64_t)row(d)[j] + (over ? (int64_t)__ldg(I.pen + j) : 0);
+        B->t_merge += clock_cycles() - tm0;
       }
       __syncthreads();
-      // Alg. 2 at j
-      int res = bellman_ford_with_allot(j, d, false, merged, allow_skip);
+      // Alg. 1 at j
+      pending_d = d;
+      pending_j = j;
+      int res = bellman_ford(j, false, merged, allow_skip);
       if (res < 0) { status = ST_ERR_INVARIANT; break; }
+      // labels converged (not skipped) and nothing applied: Alg. 4 can reuse them
+      const bool reusable = (s_misc[MS_MERGE_ANY] != 0 || !allow_skip) && res == 0;
       if (res > 0) {
         const int m = walk_path(j);
         if (m < 2) { status = ST_ERR_INVARIANT; break; }
         apply(j, false, m);
       }
-      // Alg. 3 at j when the allotment overloaded it
+      // Alg. 4 at j when the allotment overloaded it
       if (over) {
-        res = bellman_ford(j, true, true, false);
+        res = reusable && !(flags & OPT_NO_NPATH_REUSE) ? npath_from_ncyc(j)
+                                                         : bellman_ford(j, true, true, false);
         if (res < 0) { status = ST_ERR_INVARIANT; break; }
         if (res > 0) {
           const int m = walk_path(j);
@@ -642,31 +932,35 @@ struct Solver {
     cluster_sync_all();
     if (rank == 0 && tid == 0) {
       I.ctl[CTL_ROUNDS] = r;
-      I.ctl[CTL_DELTA] = delta;
-      I.ctl[CTL_FREE_TOP] = free_top;
-      I.ctl[CTL_STATUS] = status != ST_OK ? status : err0;
-      I.ctl[CTL_CYCLES] += cycles;
-      I.ctl[CTL_PATHS] += paths;
-      I.ctl[CTL_BF_CALLS] += bf_calls;
-      I.ctl[CTL_BF_SWEEPS] += bf_sweeps;
-      I.ctl[CTL_BF_MAX] = max(I.ctl[CTL_BF_MAX], bf_max);
-      I.ctl[CTL_MOVES] += moves;
-      I.ctl[CTL_NCYC_SKIPPED] += skipped;
-      I.ctl[CTL_ROWS_SCANNED] += rows;
+      I.ctl[CTL_DELTA] = B->delta;
+      I.ctl[CTL_FREE_TOP] = B->free_top;
+      I.ctl[CTL_STATUS] = status != ST_OK ? status : B->err0;
+      I.ctl[CTL_CYCLES] += B->cycles;
+      I.ctl[CTL_PATHS] += B->paths;
+      I.ctl[CTL_BF_CALLS] += B->bf_calls;
+      I.ctl[CTL_BF_SWEEPS] += B->bf_sweeps;
+      I.ctl[CTL_BF_MAX] = max(I.ctl[CTL_BF_MAX], B->bf_max);
+      I.ctl[CTL_MOVES] += B->moves;
+      I.ctl[CTL_NCYC_SKIPPED] += B->skipped;
+      I.ctl[CTL_ROWS_SCANNED] += B->rows;
+      I.ctl[CTL_T_TOTAL] += gtimer_ns() - tstart;
+      I.ctl[CTL_T_CYCLES] += clock_cycles() - cstart;
+      I.ctl[CTL_T_MERGE] += B->t_merge;
+      I.ctl[CTL_T_RELAX] += B->t_relax;
+      I.ctl[CTL_T_SYNC] += B->t_sync;
+      I.ctl[CTL_T_GATHER] += B->t_gather;
+      I.ctl[CTL_T_APPLY] += B->t_apply;
+      I.ctl[CTL_T_RESCAN] += B->t_rescan;
+      I.ctl[CTL_NPATH_REUSED] += B->npath_reused;
+      I.ctl[CTL_COL_ROWS] += B->col_rows;
+      I.ctl[CTL_FRONT_SUM] += B->front_sum;
+      for (int h = 0; h < 6; ++h) I.ctl[CTL_FRONT_HIST + h] += B->front_hist[h];
     }
   }
 
-  // The NegCycle Bellman-Ford of a round.  CTA 0 records the allotment of d
-  // (assign, member list, global load) right after the first sweep's
-  // barrier, when no CTA still reads member lists of the previous round.
-  __device__ int bellman_ford_with_allot(int32_t j, int32_t d, bool npath, bool merged,
-                                         bool allow_skip) {
-    pending_d = d;
-    pending_j = j;
-    return bellman_ford(j, npath, merged, allow_skip);
-  }
-  int32_t pending_d = -1, pending_j = -1;
-
+  // CTA 0 records the allotment of the round's unit (assign, member list,
+  // global load) right after the first sweep's barrier, when no CTA still
+  // reads member lists of the previous round.
   __device__ __forceinline__ void commit_pending() {
     if (pending_d >= 0) {
       if (rank == 0 && tid == 0) {
@@ -683,7 +977,10 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, 1)
 asral_cluster_kernel(const DevInst* __restrict__ insts, int ninst, int* work_counter, int flags) {
   extern __shared__ __align__(16) unsigned char smem[];
-  Solver<T> S;
+  __shared__ DevInst s_inst;
+  __shared__ Book s_book;
+  Solver<T> S(s_inst);
+  S.B = &s_book;
   S.tid = threadIdx.x;
   S.rank = (int)cluster_rank();
   S.C = (int)cluster_nrank();
@@ -691,6 +988,7 @@ asral_cluster_kernel(const DevInst* __restrict__ insts, int ninst, int* work_cou
   S.buf = 0;
   int64_t* s_item = reinterpret_cast<int64_t*>(smem);   // first 16 bytes: work item
   unsigned char* base = smem + 16;
+  const uint32_t avail = dyn_smem_bytes();
   for (;;) {
     if (S.rank == 0 && S.tid == 0) s_item[0] = atomicAdd(work_counter, 1);
     __syncthreads();
@@ -698,33 +996,45 @@ asral_cluster_kernel(const DevInst* __restrict__ insts, int ninst, int* work_cou
     const int item = (int)dsmem_ld64(dsmem_addr(s_item, 0));
     cluster_sync_all();
     if (item >= ninst) break;
-    S.I = insts[item];
+    if (S.tid == 0) s_inst = insts[item];
+    __syncthreads();
     S.cm = static_cast<const T*>(S.I.cm);
     S.n = S.I.n;
     S.k = S.I.k;
     S.w = own_width(S.k, S.C, Solver<T>::VPL);
+    S.ws = slice_stride(S.w, (int)sizeof(T));
     S.c0 = S.rank * S.w;
     S.c1 = min(S.k, S.c0 + S.w);
     S.wr = max(0, S.c1 - S.c0);
-    const Layout L = make_layout(S.k, S.C, Solver<T>::VPL);
+    const Layout L = make_layout(S.k, S.C, (int)sizeof(T));
+    S.tsm_on = 16 + L.total <= avail;   // same decision in every CTA of the cluster
     S.s_dist = reinterpret_cast<int64_t*>(base + L.dist);
+    S.s_hop = reinterpret_cast<int32_t*>(base + L.hop);
     S.s_load = reinterpret_cast<int32_t*>(base + L.load);
+    S.s_cap = reinterpret_cast<int32_t*>(base + L.cap);
+    S.s_pen = reinterpret_cast<int32_t*>(base + L.pen);
     S.s_front = reinterpret_cast<int32_t*>(base + L.front);
     S.s_par = reinterpret_cast<int32_t*>(base + L.par);
     S.s_outv = reinterpret_cast<int32_t*>(base + L.outv);
     S.s_outd = reinterpret_cast<int64_t*>(base + L.outd);
-    S.s_outctl = reinterpret_cast<int64_t*>(base + L.outctl);
+    S.s_inv = reinterpret_cast<int32_t*>(base + L.inv);
+    S.s_ind = reinterpret_cast<int64_t*>(base + L.ind);
+    S.s_incnt = reinterpret_cast<int32_t*>(base + L.incnt);
+    S.s_insink = reinterpret_cast<int64_t*>(base + L.insink);
     S.s_path = reinterpret_cast<int32_t*>(base + L.path);
     S.s_pathu = reinterpret_cast<int32_t*>(base + L.pathu);
     S.s_misc = reinterpret_cast<int64_t*>(base + L.misc);
     S.s_red = base + L.red;
+    S.s_tc = reinterpret_cast<typename Solver<T>::TS*>(base + L.tsm);
     if (S.I.ctl[CTL_PROLOGUE] == 0) {
+      const uint64_t t0 = gtimer_ns();
       S.prologue();
       if (S.rank == 0 && S.tid == 0) {
         S.I.ctl[CTL_FREE_TOP] = S.I.npages;
         S.I.ctl[CTL_ROUNDS] = 0;
         S.I.ctl[CTL_DELTA] = 0;
         S.I.ctl[CTL_PROLOGUE] = 1;
+        S.I.ctl[CTL_T_PROLOGUE] += gtimer_ns() - t0;
       }
       __syncthreads();
       cluster_sync_all();
@@ -734,10 +1044,11 @@ asral_cluster_kernel(const DevInst* __restrict__ insts, int ninst, int* work_cou
 }
 
 // Shared-memory bytes of one CTA for an instance with k centers on C-CTA
-// clusters (includes the 16-byte work-item slot).
-size_t solver_smem_bytes(int32_t k, int C, int elem_bytes) {
-  const int vpl = 16 / elem_bytes;
-  return 16 + make_layout(k, C, vpl).total;
+// clusters (includes the 16-byte work-item slot).  with_slice: also the
+// owned cost slice.
+size_t solver_smem_bytes(int32_t k, int C, int elem_bytes, bool with_slice) {
+  const Layout L = make_layout(k, C, elem_bytes);
+  return 16 + (with_slice ? L.total : L.base_total);
 }
 
 int solver_max_k(int C, int elem_bytes) {
@@ -780,7 +1091,8 @@ cudaError_t launch_solver(const DevInst* d_insts, int ninst, int* d_counter, int
 }
 
 // Largest number of co-resident clusters of size C for this kernel.
-int solver_max_clusters(int C, int elem_bytes, size_t smem) {
+template <typename T>
+static int max_clusters_t(int C, size_t smem) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)C, 1, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
@@ -792,24 +1104,19 @@ int solver_max_clusters(int C, int elem_bytes, size_t smem) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  auto kern = asral_cluster_kernel<T>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return -1;
+  if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                   cudaSuccess)
+    return -1;
   int num = 0;
-  cudaError_t e;
-  if (elem_bytes == 2) {
-    cudaFuncSetAttribute(asral_cluster_kernel<int16_t>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (C > 8)
-      cudaFuncSetAttribute(asral_cluster_kernel<int16_t>,
-                           cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    e = cudaOccupancyMaxActiveClusters(&num, asral_cluster_kernel<int16_t>, &cfg);
-  } else {
-    cudaFuncSetAttribute(asral_cluster_kernel<int32_t>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (C > 8)
-      cudaFuncSetAttribute(asral_cluster_kernel<int32_t>,
-                           cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    e = cudaOccupancyMaxActiveClusters(&num, asral_cluster_kernel<int32_t>, &cfg);
-  }
-  return e == cudaSuccess ? num : -1;
+  return cudaOccupancyMaxActiveClusters(&num, kern, &cfg) == cudaSuccess ? num : -1;
+}
+
+int solver_max_clusters(int C, int elem_bytes, size_t smem) {
+  return elem_bytes == 2 ? max_clusters_t<int16_t>(C, smem) : max_clusters_t<int32_t>(C, smem);
 }
 
 }  // namespace lbdd

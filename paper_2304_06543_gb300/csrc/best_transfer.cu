@@ -23,8 +23,8 @@
 namespace lbdd {
 
 constexpr int kTile = kThreads * 8;     // radix-sort tile (elements)
-constexpr int kChunk = 2048;            // rows per scan work item
-constexpr int kScanUnroll = 4;          // rows in flight per thread
+constexpr int kChunk = 512;             // rows per scan work item
+constexpr int kScanUnroll = 8;          // rows in flight per thread
 
 struct BtWorkspace {
   int32_t *k0, *v0, *k1, *v1;   // radix ping-pong
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kThreads) bt_items(const int32_t* __restrict__
 // ------------------------------------------------------------------ scan ---
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
 bt_scan_rows(const T* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
              const int32_t* __restrict__ perm,
              const int32_t* __restrict__ seg_start, const int32_t* __restrict__ seg_end,
@@ -214,37 +214,35 @@ bt_scan_rows(const T* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
 #pragma unroll
     for (int q = 0; q < VPL; ++q) { bt[q] = kTInf; bd[q] = -1; }
     if (g < R) {
-      int32_t p = r0 + g;
-      // kScanUnroll rows per step: independent 16-byte loads in flight
-      for (; p + (kScanUnroll - 1) * R < r1; p += kScanUnroll * R) {
-        int32_t d[kScanUnroll], own[kScanUnroll];
-        Vec16<T> x[kScanUnroll];
-#pragma unroll
-        for (int u = 0; u < kScanUnroll; ++u) d[u] = min((uint32_t)perm[p + u * R], (uint32_t)(n - 1));
+      // kScanUnroll rows per step: their unit ids first, then all 16-byte row
+      // loads, so that many independent loads are in flight per thread.
+      // Rows of a thread arrive in increasing d: a strict '<' keeps the
+      // lowest d among equal costs.
+      for (int32_t p = r0 + g; p < r1; p += kScanUnroll * R) {
+        int32_t d[kScanUnroll];
 #pragma unroll
         for (int u = 0; u < kScanUnroll; ++u) {
-          const T* rp = cm + (int64_t)d[u] * ld;
-          own[u] = (int32_t)rp[c];
-          x[u] = load16(rp + slot * VPL);
+          const int32_t pu = p + u * R;
+          d[u] = pu < r1 ? (int32_t)min((uint32_t)__ldg(perm + pu), (uint32_t)(n - 1)) : -1;
+        }
+        int32_t own[kScanUnroll];
+        Vec16<T> x[kScanUnroll];
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; ++u) {
+          if (d[u] >= 0) {
+            const T* rp = cm + (int64_t)d[u] * ld;
+            own[u] = (int32_t)rp[c];
+            x[u] = load16(rp + slot * VPL);
+          }
         }
 #pragma unroll
         for (int u = 0; u < kScanUnroll; ++u) {
+          if (d[u] < 0) continue;
 #pragma unroll
           for (int q = 0; q < VPL; ++q) {
             const int32_t t = (int32_t)x[u].v[q] - own[u];
             if (t < bt[q]) { bt[q] = t; bd[q] = d[u]; }
           }
-        }
-      }
-      for (; p < r1; p += R) {
-        const int32_t d = min((uint32_t)perm[p], (uint32_t)(n - 1));
-        const T* rp = cm + (int64_t)d * ld;
-        const int32_t own = (int32_t)rp[c];
-        Vec16<T> x = load16(rp + slot * VPL);
-#pragma unroll
-        for (int q = 0; q < VPL; ++q) {
-          const int32_t t = (int32_t)x.v[q] - own;
-          if (t < bt[q]) { bt[q] = t; bd[q] = d; }
         }
       }
 #pragma unroll
@@ -309,7 +307,7 @@ cudaError_t best_transfer_run(int32_t n, int32_t k, const void* cm, int elem_byt
   bt_bounds<<<grid_lin, kThreads, 0, st>>>(sk, n, k, W.seg_start, W.seg_end);
   bt_items<<<grid_lin, kThreads, 0, st>>>(W.seg_start, W.seg_end, k, W.item_off, W.t64);
   bt_scan<<<1, kThreads, 0, st>>>(W.item_off, k, W.item_off + k);
-  const int grid_scan = num_sms * 2;
+  const int grid_scan = num_sms;
   if (elem_bytes == 2)
     bt_scan_rows<int16_t><<<grid_scan, kThreads, 0, st>>>(
         static_cast<const int16_t*>(cm), ld, n, k, sv, W.seg_start, W.seg_end, W.item_off, W.t64);

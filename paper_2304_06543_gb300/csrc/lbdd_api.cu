@@ -13,7 +13,7 @@
 #include "lbdd_device.cuh"
 
 namespace lbdd {
-size_t solver_smem_bytes(int32_t k, int C, int elem_bytes);
+size_t solver_smem_bytes(int32_t k, int C, int elem_bytes, bool with_slice);
 int solver_max_k(int C, int elem_bytes);
 int solver_max_clusters(int C, int elem_bytes, size_t smem);
 cudaError_t launch_solver(const DevInst* d_insts, int ninst, int* d_counter, int C,
@@ -43,6 +43,7 @@ struct lbdd_solver {
   cudaStream_t st = nullptr;
   int cluster = 0;         // 0 = auto
   int ncyc_skip = 1;
+  int npath_reuse = 1;
   int device = 0;
   int num_sms = 0;
   std::vector<void*> allocs;
@@ -184,17 +185,26 @@ static int ingest_cm(lbdd_solver* s, const void* cm, int dtype, int is_device) {
 
 static int pick_cluster(const lbdd_solver* s) {
   if (s->cluster > 0) return s->cluster;
-  int C = (s->k + 63) / 64;
+  // about 32 owned columns per CTA: relaxation work and the exchange per
+  // Bellman-Ford sweep stay small; powers of two split the columns evenly
+  int C = (s->k + 31) / 32;
   C = std::min(16, std::max(1, C));
-  // round up to a power of two for even column splits
   int p = 1;
   while (p < C) p <<= 1;
   return std::min(16, p);
 }
 
+constexpr size_t kMaxSmem = 227 * 1024;
+
+// Dynamic shared memory for a launch: with the owned cost slice when it fits.
+static size_t launch_smem(int32_t k, int C, int elem) {
+  const size_t full = solver_smem_bytes(k, C, elem, true);
+  return full <= kMaxSmem ? full : solver_smem_bytes(k, C, elem, false);
+}
+
 static int fits(const lbdd_solver* s, int C) {
-  const size_t smem = solver_smem_bytes(s->k, C, s->elem);
-  if (smem > 227 * 1024) return 0;
+  const size_t smem = launch_smem(s->k, C, s->elem);
+  if (smem > kMaxSmem) return 0;
   const int32_t w = (s->k + C - 1) / C;
   if (w > solver_max_k(1, s->elem)) return 0;
   return solver_max_clusters(C, s->elem, smem) >= 1;
@@ -218,7 +228,7 @@ extern "C" int lbdd_create(lbdd_solver** out, int32_t n, int32_t k, const void* 
   if (rc) { delete s; return rc; }
   rc = ingest_cm(s, cm, cm_dtype, cm_is_device);
   if (rc) { free_all(s); delete s; return rc; }
-  if (solver_smem_bytes(k, 16, s->elem) > 227 * 1024) { free_all(s); delete s; return LBDD_ERR_ARG; }
+  if (launch_smem(k, 16, s->elem) > kMaxSmem) { free_all(s); delete s; return LBDD_ERR_ARG; }
   const int32_t max_pages = (n + kPage - 1) / kPage;
   const int32_t npages = max_pages + k;
   if (!rc) rc = dalloc(s, &s->cap, k);
@@ -274,6 +284,10 @@ extern "C" int lbdd_set_option(lbdd_solver* s, int option, int64_t value) {
       if (value != 0 && value != 1) return LBDD_ERR_ARG;
       s->ncyc_skip = (int)value;
       return LBDD_OK;
+    case LBDD_OPT_NPATH_REUSE:
+      if (value != 0 && value != 1) return LBDD_ERR_ARG;
+      s->npath_reuse = (int)value;
+      return LBDD_OK;
     default:
       return LBDD_ERR_ARG;
   }
@@ -299,6 +313,10 @@ static int set_target(lbdd_solver* s, int64_t max_rounds, cudaStream_t st) {
   return LBDD_OK;
 }
 
+static int solver_flags(const lbdd_solver* s) {
+  return (s->ncyc_skip ? 0 : OPT_NO_NCYC_SKIP) | (s->npath_reuse ? 0 : OPT_NO_NPATH_REUSE);
+}
+
 static int choose_cluster(lbdd_solver* s) {
   int C = pick_cluster(s);
   while (C > 1 && !fits(s, C)) C >>= 1;
@@ -311,10 +329,9 @@ extern "C" int lbdd_solve(lbdd_solver* s, int64_t max_rounds) {
   if (rc) return rc;
   const int C = choose_cluster(s);
   if (C < 1) return LBDD_ERR_ARG;
-  const size_t smem = solver_smem_bytes(s->k, C, s->elem);
+  const size_t smem = launch_smem(s->k, C, s->elem);
   CK(cudaMemsetAsync(s->counter, 0, sizeof(int32_t), s->st));
-  CK(launch_solver(s->d_inst, 1, s->counter, C, 1, s->elem, smem,
-                   s->ncyc_skip ? 0 : OPT_NO_NCYC_SKIP, s->st));
+  CK(launch_solver(s->d_inst, 1, s->counter, C, 1, s->elem, smem, solver_flags(s), s->st));
   int64_t st = 0;
   CK(cudaMemcpyAsync(&st, s->ctl + CTL_STATUS, sizeof(int64_t), cudaMemcpyDeviceToHost, s->st));
   CK(cudaStreamSynchronize(s->st));
@@ -340,8 +357,7 @@ extern "C" int lbdd_solve_batch(lbdd_solver* const* solvers, int m, int64_t max_
     if (rc) return rc;
   }
   int flags = 0;
-  for (int i = 0; i < m; ++i)
-    if (!solvers[i]->ncyc_skip) flags = OPT_NO_NCYC_SKIP;
+  for (int i = 0; i < m; ++i) flags |= solver_flags(solvers[i]);
   // one persistent launch per element size, largest instances first
   for (int elem : {2, 4}) {
     std::vector<lbdd_solver*> group;
@@ -355,11 +371,12 @@ extern "C" int lbdd_solve_batch(lbdd_solver* const* solvers, int m, int64_t max_
     for (auto* g : group) kmax = std::max(kmax, g->k);
     int C = cluster_size;
     if (C == 0) {
+      // smallest cluster whose owned cost slice fits in shared memory
       C = 1;
-      while (C < 16 && (kmax + C - 1) / C > 512) C <<= 1;
+      while (C < 16 && solver_smem_bytes(kmax, C, elem, true) > kMaxSmem) C <<= 1;
     }
-    const size_t smem = solver_smem_bytes(kmax, C, elem);
-    if (smem > 227 * 1024 || (kmax + C - 1) / C > solver_max_k(1, elem)) return LBDD_ERR_ARG;
+    const size_t smem = launch_smem(kmax, C, elem);
+    if (smem > kMaxSmem || (kmax + C - 1) / C > solver_max_k(1, elem)) return LBDD_ERR_ARG;
     const int fit = solver_max_clusters(C, elem, smem);
     if (fit < 1) return LBDD_ERR_ARG;
     int ncl = std::min<int>((int)group.size(), fit);
@@ -435,6 +452,20 @@ extern "C" int lbdd_get_stats(const lbdd_solver* s, lbdd_stats* out) {
   out->ncyc_skipped = c[CTL_NCYC_SKIPPED];
   out->rows_scanned = c[CTL_ROWS_SCANNED];
   out->cm_elem_bytes = s->elem;
+  out->prologue_ns = c[CTL_T_PROLOGUE];
+  out->rounds_ns = c[CTL_T_TOTAL];
+  // phase timers are SM cycles; scale by the measured ns per cycle of the loop
+  const double ns_per_cycle = c[CTL_T_CYCLES] > 0 ? (double)c[CTL_T_TOTAL] / c[CTL_T_CYCLES] : 0.0;
+  out->merge_ns = (int64_t)(c[CTL_T_MERGE] * ns_per_cycle);
+  out->relax_ns = (int64_t)(c[CTL_T_RELAX] * ns_per_cycle);
+  out->sync_ns = (int64_t)(c[CTL_T_SYNC] * ns_per_cycle);
+  out->gather_ns = (int64_t)(c[CTL_T_GATHER] * ns_per_cycle);
+  out->apply_ns = (int64_t)(c[CTL_T_APPLY] * ns_per_cycle);
+  out->rescan_ns = (int64_t)(c[CTL_T_RESCAN] * ns_per_cycle);
+  out->npath_reused = c[CTL_NPATH_REUSED];
+  out->col_rows = c[CTL_COL_ROWS];
+  out->front_sum = c[CTL_FRONT_SUM];
+  for (int h = 0; h < 6; ++h) out->front_hist[h] = c[CTL_FRONT_HIST + h];
   out->cluster_size = const_cast<lbdd_solver*>(s)->cluster ? s->cluster
                                                             : choose_cluster(const_cast<lbdd_solver*>(s));
   return LBDD_OK;

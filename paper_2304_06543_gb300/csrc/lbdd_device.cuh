@@ -26,8 +26,8 @@ enum CtlIndex {
   CTL_STATUS,          // 0 = ok, else an LBDD_ERR_* code
   CTL_PROLOGUE,        // 1 once s_min/order/state are initialised
   CTL_TARGET,          // rounds to reach in the current launch
-  CTL_CYCLES,          // negative cycles applied (Alg. 2)
-  CTL_PATHS,           // negative paths applied (Alg. 3)
+  CTL_CYCLES,          // negative cycles applied (Alg. 1)
+  CTL_PATHS,           // negative paths applied (Alg. 4)
   CTL_BF_CALLS,        // Bellman-Ford calls actually run
   CTL_BF_SWEEPS,       // total synchronous sweeps
   CTL_BF_MAX,          // longest call, in sweeps
@@ -35,7 +35,21 @@ enum CtlIndex {
   CTL_NCYC_SKIPPED,    // NegCycle calls skipped because T[j] did not change
   CTL_ROWS_SCANNED,    // CM rows read by segment rescans
   CTL_MAXKEY,          // largest CM(d, s_min(d)) (radix-sort width)
-  CTL_COUNT
+  CTL_T_TOTAL,         // round loop of CTA 0, globaltimer ns
+  CTL_T_CYCLES,        // the same interval in SM cycles (converts the phase timers)
+  CTL_T_PROLOGUE,      // globaltimer ns
+  // phase timers of CTA 0 in SM cycles (reported in ns by lbdd_get_stats)
+  CTL_T_MERGE,
+  CTL_T_RELAX,
+  CTL_T_SYNC,
+  CTL_T_GATHER,
+  CTL_T_APPLY,
+  CTL_T_RESCAN,
+  CTL_NPATH_REUSED,    // Alg. 4 answered from the converged Alg. 1 labels
+  CTL_COL_ROWS,        // member rows read by column-subset rescans
+  CTL_FRONT_SUM,       // sum of Bellman-Ford frontier sizes over sweeps
+  CTL_FRONT_HIST,      // 6 bins of frontier sizes: 1, 2-4, 5-16, 17-64, 65-256, >256
+  CTL_COUNT = CTL_FRONT_HIST + 6
 };
 
 // Status codes shared with include/lbdd.h.
@@ -47,6 +61,7 @@ enum : int64_t {
 // Launch-wide option bits.
 enum : int {
   OPT_NO_NCYC_SKIP = 1,   // always run the NegCycle Bellman-Ford
+  OPT_NO_NPATH_REUSE = 2, // always run the NegPath Bellman-Ford
 };
 
 // Device view of one instance.  Pointers are device memory owned by the
@@ -119,6 +134,12 @@ __device__ __forceinline__ int64_t dsmem_ld64(uint32_t addr) {
   asm volatile("ld.shared::cluster.s64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
   return v;
 }
+__device__ __forceinline__ void dsmem_st32(uint32_t addr, int32_t v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void dsmem_st64(uint32_t addr, int64_t v) {
+  asm volatile("st.shared::cluster.s64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
 
 // ------------------------------------------------------------ CM access ---
 
@@ -134,6 +155,21 @@ __device__ __forceinline__ Vec16<T> load16(const T* p) {
   int4 x = __ldg(reinterpret_cast<const int4*>(p));
   static_assert(sizeof(r) == sizeof(x), "vector size");
   *reinterpret_cast<int4*>(&r) = x;
+  return r;
+}
+
+__device__ __forceinline__ uint64_t gtimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// SM cycle counter: cheap enough to bracket every Bellman-Ford sweep.
+__device__ __forceinline__ uint64_t clock_cycles() { return (uint64_t)clock64(); }
+
+__device__ __forceinline__ uint32_t dyn_smem_bytes() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
   return r;
 }
 

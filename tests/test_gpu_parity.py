@@ -24,8 +24,9 @@ def sha(a):
     return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
 
 
-def run_gpu(lb, cm, cap, pen, rounds=-1, cluster=0, ncyc_skip=True):
-    with lb.Solver(cm, cap, pen, cluster=cluster, ncyc_skip=ncyc_skip) as s:
+def run_gpu(lb, cm, cap, pen, rounds=-1, cluster=0, ncyc_skip=True, npath_reuse=True):
+    with lb.Solver(cm, cap, pen, cluster=cluster, ncyc_skip=ncyc_skip,
+                   npath_reuse=npath_reuse) as s:
         s.solve(rounds)
         return s.assignment(), s.objective, s.loads(), s.stats(), s.table()
 
@@ -54,11 +55,11 @@ def test_tiny_matches_golden(gpu_lib, cluster):
 def test_tiny_without_skip_and_int32_storage(gpu_lib):
     inst = L.make_named("tiny")
     ref = oracle.asral(inst.cm, inst.cap, inst.pen)
-    out = run_gpu(gpu_lib, inst.cm, inst.cap, inst.pen, ncyc_skip=False)
+    out = run_gpu(gpu_lib, inst.cm, inst.cap, inst.pen, ncyc_skip=False, npath_reuse=False)
     assert_same(out, ref, inst.k)
-    # every Alg. 2 call ran Bellman-Ford: same call count as the oracle
+    # every Alg. 1 and Alg. 4 call ran Bellman-Ford: same call count as the oracle
     assert out[3].bf_calls == ref.stats["bf_calls"]
-    assert out[3].ncyc_skipped == 0
+    assert out[3].ncyc_skipped == 0 and out[3].npath_reused == 0
     # a CM too wide for int16 stays int32 and gives the same result
     cm = inst.cm.astype(np.int32) + 40000
     ref2 = oracle.asral(cm, inst.cap, inst.pen)
@@ -84,6 +85,21 @@ def test_random_small_instances(gpu_lib, seed):
         tc, td = out[4]
         tc_ref = np.where(tc_ref >= oracle.INF, 2**31 - 1, tc_ref)
         assert np.array_equal(tc, tc_ref) and np.array_equal(td, td_ref)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_shortcuts_do_not_change_results(gpu_lib, seed):
+    """Skipping Alg. 1 when T is unchanged and answering Alg. 4 from Alg. 1's
+    labels must give exactly the same allotment as running every
+    Bellman-Ford (and as the oracle)."""
+    inst = L.random_small(6100 + seed, n=400, k=[6, 23, 40][seed % 3], cm_max=[6, 40][seed % 2],
+                          cap_frac=0.6, pen=(1, 30))
+    ref = oracle.asral(inst.cm, inst.cap, inst.pen)
+    outs = [run_gpu(gpu_lib, inst.cm, inst.cap, inst.pen, cluster=c, ncyc_skip=a, npath_reuse=b)
+            for c in (1, 2) for a in (True, False) for b in (True, False)]
+    for out in outs:
+        assert_same(out, ref, inst.k)
+    assert outs[0][3].npath_reused > 0
 
 
 def test_single_center_and_ample_capacity(gpu_lib):

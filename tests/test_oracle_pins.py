@@ -39,7 +39,7 @@ def test_asral_never_below_optimum_and_reaches_it(mode):
     With constant per-unit penalties every refinement is a shortest
     augmenting path of a convex-cost flow, and on all seeded instances here
     the value equals the optimum; a dropped term, a sign or index slip in the
-    graphs of Defs. 5/6 breaks the equality."""
+    graphs of Defs. 9/10 breaks the equality."""
     for s in range(40):
         n = [8, 20, 45][s % 3]
         k = [2, 3, 5, 7][s % 4]
@@ -129,7 +129,7 @@ def test_single_center_closed_form():
 
 
 def test_smin_and_order_definition():
-    """Alg. 1 line 1: lowest-index row minimum; order (cost, d) ascending,
+    """Alg. 2, first step: lowest-index row minimum; order (cost, d) ascending,
     checked against numpy's argmin (first occurrence) and lexsort."""
     J = small(1700, 500, 9, cm_max=5)
     smin, order = oracle.smin_order(J.cm)
