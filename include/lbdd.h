@@ -195,6 +195,30 @@ int lbdd_best_transfer(int32_t n, int32_t k, const void* cm_dev, int cm_dtype, i
                        const int32_t* assign_dev, int32_t* tc_dev, int32_t* td_dev,
                        void* workspace, size_t workspace_bytes, void* stream);
 
+/* The same table as lbdd_best_transfer, computed without allocating any
+ * device memory.  The paper has no counterpart: this call exists for callers
+ * that must not call cudaMalloc when they need the table, because cudaMalloc
+ * can synchronise the whole device or because their device memory is fixed
+ * in advance by a host application.  Instead of a caller workspace, the
+ * scratch is one file-scope device array of 64 MiB, reserved on every GPU that
+ * loads this library until the process exits.
+ *   Arguments as for lbdd_best_transfer (inputs and outputs are still the
+ *   caller's device buffers), without the workspace.
+ *   Limit: lbdd_best_transfer_workspace(n, k) must not exceed 64 MiB, else
+ *   LBDD_ERR_BUDGET is returned and nothing is launched (the city-scale
+ *   200,000 x 500 case needs about 5 MiB).
+ *   The first call on each device looks up the device address of the array
+ *   (with that device current); make that first call before any stream
+ *   capture.
+ *   All calls on a device share the one array and every call rewrites what
+ *   it reads, so consecutive calls are independent; calls whose work overlaps
+ *   on the GPU (different streams, or different host threads) race on it and
+ *   must be serialised by the caller.
+ * Errors: LBDD_ERR_ARG, LBDD_ERR_BUDGET, LBDD_ERR_NODEV, LBDD_ERR_CUDA. */
+int lbdd_best_transfer_noalloc(int32_t n, int32_t k, const void* cm_dev, int cm_dtype, int64_t ld,
+                               const int32_t* assign_dev, int32_t* tc_dev, int32_t* td_dev,
+                               void* stream);
+
 /* Row pitch (elements) that lbdd_create uses for a CM of k columns, and the
  * device pointer / pitch of a solver's stored CM (for lbdd_best_transfer). */
 int64_t lbdd_cm_pitch(int32_t k, int cm_dtype);
