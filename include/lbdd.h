@@ -79,6 +79,10 @@ typedef struct lbdd_stats {
   int64_t gather_ns;        /* Bellman-Ford exchange of label changes */
   int64_t apply_ns;         /* path application (member lists, loads) */
   int64_t rescan_ns;        /* segment rescans of the best-transfer rows */
+  int64_t relax_loop_ns;    /* part of relax_ns: the relaxation loop itself */
+  int64_t relax_reduce_ns;  /* part of relax_ns: loop + cross-warp reduction and record */
+  int64_t cost_slice_in_smem; /* 1 if the last solve kept each CTA's best-transfer cost
+                                 columns in shared memory */
   int64_t npath_reused;     /* Alg. 4 calls answered from the labels of an Alg. 1
                                Bellman-Ford that applied nothing (exact: same graph
                                except for the sink edges) */
@@ -93,6 +97,8 @@ typedef enum lbdd_option {
   LBDD_OPT_NCYC_SKIP = 2,   /* 1 (default): skip Alg. 1's Bellman-Ford when the new
                                unit lowers no best-transfer cost (exact by Lemma 1);
                                0: always run it */
+  LBDD_OPT_TC_SMEM = 4,     /* 1 (default): keep each CTA's best-transfer cost columns in
+                               shared memory when they fit; 0: read them from global memory */
   LBDD_OPT_NPATH_REUSE = 3, /* 1 (default): answer Alg. 4 from the converged labels of
                                an Alg. 1 run that applied nothing; 0: always run a
                                separate Bellman-Ford */

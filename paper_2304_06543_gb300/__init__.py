@@ -28,7 +28,7 @@ OK = 0
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_INVARIANT, ERR_STATE, ERR_NODEV, ERR_BUDGET = \
     -1, -2, -3, -4, -5, -6, -7, -8
 CM_I32, CM_I16 = 0, 1
-OPT_CLUSTER, OPT_NCYC_SKIP, OPT_NPATH_REUSE = 1, 2, 3
+OPT_CLUSTER, OPT_NCYC_SKIP, OPT_NPATH_REUSE, OPT_TC_SMEM = 1, 2, 3, 4
 TINF = 2**31 - 1
 
 _lib = None
@@ -47,7 +47,8 @@ _STAT_FIELDS = (
     "rounds", "cycles_applied", "paths_applied", "bf_calls", "bf_sweeps", "bf_max_sweeps",
     "moves", "ncyc_skipped", "rows_scanned", "cm_elem_bytes", "cluster_size",
     "prologue_ns", "rounds_ns", "merge_ns", "relax_ns", "sync_ns", "gather_ns", "apply_ns",
-    "rescan_ns", "npath_reused", "col_rows", "front_sum")
+    "rescan_ns", "relax_loop_ns", "relax_reduce_ns", "cost_slice_in_smem", "npath_reused",
+    "col_rows", "front_sum")
 
 
 class _Stats(ctypes.Structure):
@@ -143,6 +144,9 @@ class Stats:
     gather_ns: int
     apply_ns: int
     rescan_ns: int
+    relax_loop_ns: int
+    relax_reduce_ns: int
+    cost_slice_in_smem: int
     npath_reused: int
     col_rows: int
     front_sum: int

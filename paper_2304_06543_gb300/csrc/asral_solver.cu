@@ -32,7 +32,7 @@
 namespace lbdd {
 
 struct Layout {
-  uint32_t dist, hop, load, cap, pen, front, par, outv, outd, inv, ind, incnt, insink, path, pathu,
+  uint32_t dist, hop, load, cap, pen, front, par, outk, ink, incnt, insink, npart, path, pathu,
       misc, red, tsm, base_total, total;
 };
 
@@ -65,14 +65,13 @@ __host__ __device__ inline Layout make_layout(int32_t k, int32_t C, int32_t elem
   L.load = o;   o = align16(o + 4u * ku);
   L.cap = o;    o = align16(o + 4u * ku);
   L.pen = o;    o = align16(o + 4u * ku);
-  L.front = o;  o = align16(o + 4u * (ku + 1));
+  L.front = o;  o = align16(o + 8u * (ku + 1));       // frontier keys of the current sweep
   L.par = o;    o = align16(o + 4u * w);
-  L.outv = o;   o = align16(o + 4u * w);              // this sweep's own changes
-  L.outd = o;   o = align16(o + 8u * w);
-  L.inv = o;    o = align16(o + 2u * Cu * w * 4u);     // inbox [2][C][w] nodes
-  L.ind = o;    o = align16(o + 2u * Cu * w * 8u);     // inbox [2][C][w] labels
+  L.outk = o;   o = align16(o + 8u * w);              // this sweep's own changes (keys)
+  L.ink = o;    o = align16(o + 2u * Cu * w * 8u);     // inbox [2][C][w] keys = next frontier
   L.incnt = o;  o = align16(o + 2u * Cu * 2u * 4u);    // inbox [2][C] {count, merge flag}
   L.insink = o; o = align16(o + 2u * 4u * 8u);         // inbox [2] sink record
+  L.npart = o;  o = align16(o + Cu * 16u);             // per-CTA partial minima
   L.path = o;   o = align16(o + 4u * (ku + 2));
   L.pathu = o;  o = align16(o + 4u * (ku + 2));
   L.misc = o;   o = align16(o + 8u * 16u);
@@ -86,14 +85,14 @@ __host__ __device__ inline Layout make_layout(int32_t k, int32_t C, int32_t elem
 // Sink record of an inbox buffer.
 enum { SK_CHANGED = 0, SK_DIST, SK_PAR };
 // Slots of the per-CTA scalar block.
-enum { MS_NFRONT = 0, MS_SINK_DIST, MS_SINK_PAR, MS_CNT, MS_TOTAL, MS_PATHLEN, MS_SINK_CHG,
-       MS_MERGE_ANY, MS_OWN_SINK_CHG, MS_OWN_SINK_DIST, MS_OWN_SINK_PAR, MS_NAFF };
+enum { MS_SINK_DIST = 0, MS_SINK_PAR, MS_LCNT0, MS_LCNT1, MS_PATHLEN, MS_OWN_SINK_CHG0,
+       MS_OWN_SINK_CHG1, MS_OWN_SINK_DIST, MS_OWN_SINK_PAR, MS_NAFF, MS_MERGE_ANY };
 
 // Counters and timers kept by thread 0 of CTA 0 (shared memory, so that
 // they cost no registers in the other threads).
 struct Book {
   int64_t delta, free_top, cycles, paths, bf_calls, bf_sweeps, bf_max, moves, skipped, rows;
-  int64_t t_merge, t_relax, t_sync, t_gather, t_apply, t_rescan;
+  int64_t t_merge, t_relax, t_sync, t_gather, t_apply, t_rescan, t_rloop, t_rred;
   int64_t npath_reused, col_rows, front_sum, front_hist[6];
   int64_t err0;   // a guard tripped (corrupt state; never expected)
 };
@@ -112,19 +111,18 @@ struct Solver {
   int tid;
   int flags;
   bool tsm_on;        // owned cost slice resident in shared memory
-  int64_t* s_dist;    // label replica of every node
-  int32_t* s_hop;     // sweep of each node's last label change (replica)
+  int64_t* s_dist;    // labels of the owned columns (and 0 at the source)
+  int32_t* s_hop;     // sweep of each owned column's last label change
   int32_t* s_load;
   int32_t* s_cap;     // capacity replica
   int32_t* s_pen;     // penalty replica
-  int32_t* s_front;
+  uint64_t* s_front;  // frontier keys ((label + 2^47) << 16 | node) of the current sweep
   int32_t* s_par;     // parents of the owned columns
-  int32_t* s_outv;    // [w] owned columns improved in this sweep
-  int64_t* s_outd;    // [w] their new labels
-  int32_t* s_inv;     // inbox [2][C][w]: nodes changed by CTA r in a sweep
-  int64_t* s_ind;     // inbox [2][C][w]: their new labels
+  uint64_t* s_outk;   // [w] keys of the owned columns improved in this sweep
+  uint64_t* s_ink;    // inbox [2][C][w]: keys ((label + 2^47) << 16 | node) pushed by CTA r
   int32_t* s_incnt;   // inbox [2][C][2]: {count, merge flag} from CTA r
   int64_t* s_insink;  // inbox [2][4]: sink record from the owner of column j
+  int64_t* s_npart;   // [C][2]: per-CTA partial minima (label; hop << 16 | node)
   int32_t* s_path;
   int32_t* s_pathu;
   int64_t* s_misc;
@@ -407,65 +405,90 @@ struct Solver {
   // -------------------------------------------------------- Bellman-Ford --
   // Lexicographic minimum of (label[u] + weight(u, v), u) over this
   // lane's share of the frontier (entries g, g+G, ...).
-  // Lexicographic minimum of (label[u] + weight(u, v), u) over the frontier
+  // A frontier entry packs (label, node) so that one unsigned 64-bit minimum
+  // is the lexicographic minimum of (label, node): node in the low 16 bits
+  // (k <= 65535), label + 2^47 above it (labels are sums of at most k+1 edge
+  // weights below 2^31 in magnitude, so |label| < 2^47).  Adding an edge
+  // weight t shifted by 16 bits keeps the node bits intact.
+  static __device__ __forceinline__ uint64_t pack_key(int64_t label, int32_t node) {
+    return ((uint64_t)(label + ((int64_t)1 << 47)) << 16) | (uint32_t)node;
+  }
+  static __device__ __forceinline__ int64_t key_label(uint64_t key) {
+    return (int64_t)(key >> 16) - ((int64_t)1 << 47);
+  }
+
+  // Minimum packed key of (label[u] + weight(u, v), u) over the frontier
   // entries slice, slice+step, ...  Lanes of a warp hold consecutive owned
-  // columns and walk the same frontier entries, so the label read is a
+  // columns and walk the same frontier entries, so the key read is a
   // broadcast and the cost reads are consecutive (no bank conflicts).
-  __device__ __forceinline__ void relax_column(int cl, bool valid, int slice, int step,
-                                               int nfront, int32_t j, bool npath,
-                                               int32_t pen_j, int64_t& bc, int32_t& bu) const {
-    bc = kDInf;
-    bu = INT32_MAX;
+  __device__ __forceinline__ uint64_t relax_column(int cl, bool valid, int slice, int step,
+                                                   int nfront, int32_t j, bool npath,
+                                                   int32_t pen_j) const {
+    uint64_t best = ~0ull;
     const int v = c0 + cl;
-    const bool pen_edge = valid && (v == j) && npath;
+    if (!valid) return best;
+    if (v == j && npath) {             // Def. 10 (c): q_u() - q_{s*}()
+      for (int f = slice; f < nfront; f += step) {
+        const uint64_t key = s_front[f];
+        const int32_t u = (int32_t)(key & 0xffffu);
+        if (u == j) continue;
+        const int64_t t = (int64_t)(s_load[u] >= s_cap[u] ? s_pen[u] : 0) - pen_j;
+        best = min(best, key + ((uint64_t)t << 16));
+      }
+      return best;
+    }
+    // transfer edges u -> v (v == j: into s*in)
     constexpr int U = 4;
     int f = slice;
-    for (; f + (U - 1) * step < nfront; f += U * step) {
-      int32_t u[U], t[U];
-      int64_t du[U];
+    if (tsm_on) {
+      const TS* col = s_tc + cl;
+      for (; f + (U - 1) * step < nfront; f += U * step) {
+        uint64_t key[U];
+        int32_t t[U];
 #pragma unroll
-      for (int q = 0; q < U; ++q) u[q] = s_front[f + q * step];
+        for (int q = 0; q < U; ++q) key[q] = s_front[f + q * step];
 #pragma unroll
-      for (int q = 0; q < U; ++q) {
-        du[q] = s_dist[u[q]];
-        if (pen_edge)                 // Def. 10 (c): q_u() - q_{s*}()
-          t[q] = (u[q] == j) ? kTInf : (s_load[u[q]] >= s_cap[u[q]] ? s_pen[u[q]] : 0) - pen_j;
-        else                          // transfer edge u -> v (v == j: into s*in)
-          t[q] = valid ? own_cost(u[q], cl) : kTInf;
+        for (int q = 0; q < U; ++q) t[q] = (int32_t)col[(int32_t)(key[q] & 0xffffu) * ws];
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+          if (t[q] != kTsInf) best = min(best, key[q] + ((uint64_t)(int64_t)t[q] << 16));
       }
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        if (t[q] == kTInf) continue;
-        const int64_t c = du[q] + t[q];
-        if (c < bc || (c == bc && u[q] < bu)) { bc = c; bu = u[q]; }
+      for (; f < nfront; f += step) {
+        const uint64_t key = s_front[f];
+        const int32_t t = (int32_t)col[(int32_t)(key & 0xffffu) * ws];
+        if (t != kTsInf) best = min(best, key + ((uint64_t)(int64_t)t << 16));
+      }
+    } else {
+      const int32_t* col = I.tc + c0 + cl;
+      for (; f < nfront; f += step) {
+        const uint64_t key = s_front[f];
+        const int32_t t = col[(int64_t)(key & 0xffffu) * k];
+        if (t != kTInf) best = min(best, key + ((uint64_t)(int64_t)t << 16));
       }
     }
-    for (; f < nfront; f += step) {
-      const int32_t u = s_front[f];
-      int32_t t;
-      if (pen_edge) t = (u == j) ? kTInf : (s_load[u] >= s_cap[u] ? s_pen[u] : 0) - pen_j;
-      else t = valid ? own_cost(u, cl) : kTInf;
-      if (t == kTInf) continue;
-      const int64_t c = s_dist[u] + t;
-      if (c < bc || (c == bc && u < bu)) { bc = c; bu = u; }
-    }
+    return best;
   }
 
   // Strict improvement of owned column cl: record it in the local out list
   // (pushed to every CTA after the relaxation) or as the sink's new label.
-  __device__ __forceinline__ void record(int cl, int64_t bc, int32_t bu, int32_t j,
-                                         int64_t sink_dist) {
+  // Only the owner reads and writes the label of an owned column.
+  __device__ __forceinline__ void record(int cl, uint64_t best, int32_t j, int64_t sink_dist,
+                                         int sweep, int pb) {
+    if (best == ~0ull) return;
+    const int64_t bc = key_label(best);
+    const int32_t bu = (int32_t)(best & 0xffffu);
     const int v = c0 + cl;
     const int64_t cur = (v == j) ? sink_dist : s_dist[v];
     if (bc < cur) {
       if (v == j) {
-        s_misc[MS_OWN_SINK_CHG] = 1;
+        s_misc[MS_OWN_SINK_CHG0 + pb] = 1;
         s_misc[MS_OWN_SINK_DIST] = bc;
         s_misc[MS_OWN_SINK_PAR] = bu;
       } else {
-        const int at = atomicAdd(reinterpret_cast<int*>(&s_misc[MS_CNT]), 1);
-        s_outv[at] = v;
-        s_outd[at] = bc;
+        const int at = atomicAdd(reinterpret_cast<int*>(&s_misc[MS_LCNT0 + pb]), 1);
+        s_outk[at] = pack_key(bc, v);
+        s_dist[v] = bc;
+        s_hop[v] = sweep;
         s_par[cl] = bu;
       }
     }
@@ -488,17 +511,17 @@ struct Solver {
   // < 0 on a broken invariant.  `merged` says whether this CTA's merge of
   // the round's unit lowered a cost of row j (NegCycle only).
   __device__ int bellman_ford(int32_t j, bool npath, bool merged, bool allow_skip) {
-    for (int v = tid; v < k; v += kThreads) {
-      s_dist[v] = (v == j) ? 0 : kDInf;
-      s_hop[v] = (v == j) ? 0 : -1;
+    for (int cl = tid; cl < w; cl += kThreads) {
+      const int v = c0 + cl;
+      if (v < k) { s_dist[v] = (v == j) ? 0 : kDInf; s_hop[v] = (v == j) ? 0 : -1; }
+      s_par[cl] = -1;
     }
-    for (int v = tid; v < w; v += kThreads) s_par[v] = -1;
     if (tid == 0) {
-      s_front[0] = j;
-      s_misc[MS_NFRONT] = 1;
-      s_misc[MS_SINK_DIST] = kDInf;
-      s_misc[MS_SINK_PAR] = -1;
-      s_misc[MS_CNT] = 0;
+      s_dist[j] = 0;
+      s_hop[j] = 0;
+      s_front[0] = pack_key(0, j);
+      s_misc[MS_LCNT0 + buf] = 0;
+      s_misc[MS_OWN_SINK_CHG0 + buf] = 0;
     }
     __syncthreads();
     const int owner_j = j / w;
@@ -508,65 +531,57 @@ struct Solver {
     const int CB = max(1, (wr + 31) / 32);
     const int WPB = max(1, kWarps / CB);
     const int lane = tid & 31, warp = tid >> 5;
-    int* s_cntloc = reinterpret_cast<int*>(&s_misc[MS_CNT]);
-    int32_t* s_cnt = reinterpret_cast<int32_t*>(s_red);                   // [C+1] prefix
-    int64_t* red_c = reinterpret_cast<int64_t*>(s_red + 256);             // [WPB][CB*32]
-    int32_t* red_u = reinterpret_cast<int32_t*>(s_red + 256 + 8 * kThreads);
+    uint64_t* red_k = reinterpret_cast<uint64_t*>(s_red + 256);           // [WPB][CB*32]
+    // every thread keeps the same copy of the sink label, the frontier size
+    // and the previous inbox buffer; they change only at cluster barriers
+    int64_t sink_dist = kDInf;
+    int32_t sink_par = -1;
+    int nfront = 1;
     int result = 0;
+    bool skipped_bf = false;
     for (int sweep = 1;; ++sweep) {
       const uint64_t t0 = timer() ? clock_cycles() : 0;
-      const int nfront = (int)s_misc[MS_NFRONT];
-      const int64_t sink_dist = s_misc[MS_SINK_DIST];
+      const int pb = buf;                      // buffer written in this sweep
       if (timer()) {
         B->front_sum += nfront;
         B->front_hist[nfront <= 1 ? 0 : nfront <= 4 ? 1 : nfront <= 16 ? 2 : nfront <= 64 ? 3
                       : nfront <= 256 ? 4 : 5]++;
       }
-      int32_t* inv = s_inv + buf * C * w;
-      int64_t* ind = s_ind + buf * C * w;
-      int32_t* incnt = s_incnt + buf * C * 2;
-      int64_t* insink = s_insink + buf * 4;
-      if (tid == 0) s_misc[MS_OWN_SINK_CHG] = 0;
-      __syncthreads();
       // relax all edges out of the frontier into the owned columns
       if (WPB > 1) {
         const int blk = warp / WPB, slice = warp % WPB;
         if (blk < CB) {
           const int cl = blk * 32 + lane;
-          int64_t bc;
-          int32_t bu;
-          relax_column(cl, cl < wr, slice, WPB, nfront, j, npath, pen_j, bc, bu);
-          red_c[slice * CB * 32 + cl] = bc;
-          red_u[slice * CB * 32 + cl] = bu;
+          red_k[slice * CB * 32 + cl] = relax_column(cl, cl < wr, slice, WPB, nfront, j, npath,
+                                                     pen_j);
         }
         __syncthreads();
+        if (timer()) B->t_rloop += clock_cycles() - t0;
         for (int cl = tid; cl < wr; cl += kThreads) {
-          int64_t bc = kDInf;
-          int32_t bu = INT32_MAX;
-          for (int sl = 0; sl < WPB; ++sl) {
-            const int64_t c = red_c[sl * CB * 32 + cl];
-            const int32_t u = red_u[sl * CB * 32 + cl];
-            if (c < bc || (c == bc && u < bu)) { bc = c; bu = u; }
-          }
-          record(cl, bc, bu, j, sink_dist);
+          uint64_t best = ~0ull;
+          for (int sl = 0; sl < WPB; ++sl) best = min(best, red_k[sl * CB * 32 + cl]);
+          record(cl, best, j, sink_dist, sweep, pb);
         }
       } else {
         for (int blk = warp; blk < CB; blk += kWarps) {
           const int cl = blk * 32 + lane;
-          int64_t bc;
-          int32_t bu;
-          relax_column(cl, cl < wr, 0, 1, nfront, j, npath, pen_j, bc, bu);
-          if (cl < wr) record(cl, bc, bu, j, sink_dist);
+          const uint64_t best = relax_column(cl, cl < wr, 0, 1, nfront, j, npath, pen_j);
+          if (cl < wr) record(cl, best, j, sink_dist, sweep, pb);
         }
       }
       __syncthreads();
-      // push this CTA's changes into every CTA's inbox (all threads help)
+      if (timer()) B->t_rred += clock_cycles() - t0;
+      // push this CTA's changes into every CTA's inbox buffer pb (all threads
+      // help), then prepare the other buffer's local counters for the next
+      // sweep; both happen before the barrier, so no sweep can see them early
       {
-        const int cnt = *s_cntloc;
+        uint64_t* ink = s_ink + pb * C * w;
+        int32_t* incnt = s_incnt + pb * C * 2;
+        int64_t* insink = s_insink + pb * 4;
+        const int cnt = (int)s_misc[MS_LCNT0 + pb];
         for (int i = tid; i < cnt * C; i += kThreads) {
           const int e = i / C, r = i - e * C;
-          dsmem_st32(dsmem_addr(inv + rank * w + e, r), s_outv[e]);
-          dsmem_st64(dsmem_addr(ind + rank * w + e, r), s_outd[e]);
+          dsmem_st64(dsmem_addr(ink + rank * w + e, r), (int64_t)s_outk[e]);
         }
         if (tid >= kThreads - 32 && tid - (kThreads - 32) < C) {
           const uint32_t r = tid - (kThreads - 32);
@@ -575,52 +590,36 @@ struct Solver {
         }
         if (rank == owner_j && tid >= kThreads - 64 && tid - (kThreads - 64) < C) {
           const uint32_t r = tid - (kThreads - 64);
-          dsmem_st64(dsmem_addr(insink + SK_CHANGED, r), s_misc[MS_OWN_SINK_CHG]);
+          dsmem_st64(dsmem_addr(insink + SK_CHANGED, r), s_misc[MS_OWN_SINK_CHG0 + pb]);
           dsmem_st64(dsmem_addr(insink + SK_DIST, r), s_misc[MS_OWN_SINK_DIST]);
           dsmem_st64(dsmem_addr(insink + SK_PAR, r), s_misc[MS_OWN_SINK_PAR]);
+        }
+        if (tid == 0) {
+          s_misc[MS_LCNT0 + (pb ^ 1)] = 0;
+          s_misc[MS_OWN_SINK_CHG0 + (pb ^ 1)] = 0;
         }
       }
       const uint64_t t1 = timer() ? clock_cycles() : 0;
       cluster_sync_all();
       const uint64_t t2 = timer() ? clock_cycles() : 0;
       commit_pending();
-      // apply the local inbox (same order in every CTA)
-      if (tid < 32) {
-        int32_t cnt = 0, mg = 0;
-        if (lane < C) { cnt = incnt[lane * 2]; mg = incnt[lane * 2 + 1]; }
-        int32_t inc = cnt;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const int32_t o = __shfl_up_sync(0xffffffffu, inc, off);
-          if (lane >= off) inc += o;
+      // read the local inbox (every thread, same values in every CTA)
+      const int32_t* incnt = s_incnt + pb * C * 2;
+      const int64_t* insink = s_insink + pb * 4;
+      int total = 0;
+      bool any_merge = false;
+      for (int r = 0; r < C; ++r) { total += incnt[2 * r]; any_merge |= incnt[2 * r + 1] != 0; }
+      const bool sink_chg = insink[SK_CHANGED] != 0;
+      if (sink_chg) { sink_dist = insink[SK_DIST]; sink_par = (int32_t)insink[SK_PAR]; }
+      nfront = total;
+      // the inbox segments become the next frontier (a local copy)
+      {
+        const uint64_t* ink = s_ink + pb * C * w;
+        int r = 0, base = 0, cr = C > 0 ? incnt[0] : 0;
+        for (int i = tid; i < total; i += kThreads) {
+          while (i >= base + cr) { base += cr; ++r; cr = incnt[2 * r]; }
+          s_front[i] = ink[r * w + (i - base)];
         }
-        const unsigned any = __ballot_sync(0xffffffffu, mg != 0);
-        if (lane < C) s_cnt[lane] = inc - cnt;
-        if (lane == C - 1) { s_cnt[C] = inc; s_misc[MS_TOTAL] = inc; }
-        if (lane == 0) {
-          s_misc[MS_MERGE_ANY] = any ? 1 : 0;
-          const int64_t chg = insink[SK_CHANGED];
-          s_misc[MS_SINK_CHG] = chg;
-          if (chg) {
-            s_misc[MS_SINK_DIST] = insink[SK_DIST];
-            s_misc[MS_SINK_PAR] = insink[SK_PAR];
-          }
-        }
-      }
-      __syncthreads();
-      const int total = (int)s_misc[MS_TOTAL];
-      for (int i = tid; i < total; i += kThreads) {
-        int r = 0;
-        while (s_cnt[r + 1] <= i) ++r;
-        const int li = i - s_cnt[r];
-        const int32_t v = inv[r * w + li];
-        s_front[i] = v;
-        s_dist[v] = ind[r * w + li];
-        s_hop[v] = sweep;
-      }
-      if (tid == 0) {
-        s_misc[MS_NFRONT] = total;
-        s_misc[MS_CNT] = 0;
       }
       __syncthreads();
       if (timer()) {
@@ -630,12 +629,13 @@ struct Solver {
         B->t_gather += t3 - t2;
       }
       buf ^= 1;
-      const bool sink_chg = s_misc[MS_SINK_CHG] != 0;
-      if (sweep == 1 && allow_skip && s_misc[MS_MERGE_ANY] == 0) {
+      if (sweep == 1 && allow_skip && !any_merge) {
         // T is unchanged since the last round, whose Gamma had no negative
         // cycle (Lemmas 1/2): the NegCycle sink label cannot be negative.
         if (rank == 0 && tid == 0) B->skipped++;
-        return 0;
+        result = 0;
+        skipped_bf = true;
+        break;
       }
       if (total == 0 && !sink_chg) {
         if (rank == 0 && tid == 0) {
@@ -643,11 +643,17 @@ struct Solver {
           B->bf_sweeps += sweep;
           B->bf_max = max(B->bf_max, (int64_t)sweep);
         }
-        result = s_misc[MS_SINK_DIST] < 0 ? 1 : 0;
+        result = sink_dist < 0 ? 1 : 0;
         break;
       }
       if (sweep >= k + 1) { result = -1; break; }
     }
+    if (tid == 0) {
+      s_misc[MS_SINK_DIST] = sink_dist;
+      s_misc[MS_SINK_PAR] = sink_par;
+      s_misc[MS_MERGE_ANY] = skipped_bf ? 0 : 1;   // 1: the labels converged
+    }
+    __syncthreads();
     return result;
   }
 
@@ -658,40 +664,53 @@ struct Solver {
   // parent follow from one reduction: the synchronous sweep reaches the
   // minimum first through the predecessors u of smallest hop count (the
   // sweep of u's last change), and among those takes the lowest index.
-  // Every CTA computes the same result from its replicas.  Returns 1 if the
+  // Each CTA reduces over the columns it owns, the partial minima are
+  // exchanged, and every CTA combines the same partials.  Returns 1 if the
   // sink label is negative.
   __device__ int npath_from_ncyc(int32_t j) {
     const int32_t pen_j = __ldg(I.pen + j);
     int64_t bc = kDInf;
-    int32_t bh = INT32_MAX, bu = INT32_MAX;
-    for (int u = tid; u < k; u += kThreads) {
+    uint32_t bhu = 0xffffffffu;   // hop << 16 | node
+    auto better = [](int64_t c, uint32_t hu, int64_t bc_, uint32_t bhu_) {
+      return c < bc_ || (c == bc_ && hu < bhu_);
+    };
+    for (int cl = tid; cl < wr; cl += kThreads) {
+      const int u = c0 + cl;
       if (u == j || s_dist[u] >= kDInf) continue;
       const int64_t c = s_dist[u] + (int64_t)(s_load[u] >= s_cap[u] ? s_pen[u] : 0) - pen_j;
-      const int32_t h = s_hop[u];
-      if (c < bc || (c == bc && (h < bh || (h == bh && u < bu)))) { bc = c; bh = h; bu = u; }
+      const uint32_t hu = ((uint32_t)s_hop[u] << 16) | (uint32_t)u;
+      if (better(c, hu, bc, bhu)) { bc = c; bhu = hu; }
     }
     for (int off = 16; off > 0; off >>= 1) {
       const int64_t oc = __shfl_xor_sync(0xffffffffu, bc, off);
-      const int32_t oh = __shfl_xor_sync(0xffffffffu, bh, off);
-      const int32_t ou = __shfl_xor_sync(0xffffffffu, bu, off);
-      if (oc < bc || (oc == bc && (oh < bh || (oh == bh && ou < bu)))) { bc = oc; bh = oh; bu = ou; }
+      const uint32_t ohu = __shfl_xor_sync(0xffffffffu, bhu, off);
+      if (better(oc, ohu, bc, bhu)) { bc = oc; bhu = ohu; }
     }
     int64_t* rc = reinterpret_cast<int64_t*>(s_red);
-    int32_t* rh = reinterpret_cast<int32_t*>(s_red + 8 * kWarps);
-    int32_t* ru = rh + kWarps;
-    if ((tid & 31) == 0) { rc[tid >> 5] = bc; rh[tid >> 5] = bh; ru[tid >> 5] = bu; }
+    uint32_t* rhu = reinterpret_cast<uint32_t*>(s_red + 8 * kWarps);
+    if ((tid & 31) == 0) { rc[tid >> 5] = bc; rhu[tid >> 5] = bhu; }
     __syncthreads();
+    if (tid < C) {   // thread r sends this CTA's partial to CTA r
+      for (int i = 0; i < kWarps; ++i)
+        if (better(rc[i], rhu[i], bc, bhu)) { bc = rc[i]; bhu = rhu[i]; }
+      dsmem_st64(dsmem_addr(s_npart + 2 * rank, tid), bc);
+      dsmem_st64(dsmem_addr(s_npart + 2 * rank + 1, tid), (int64_t)bhu);
+    }
+    cluster_sync_all();
+    bc = kDInf;
+    bhu = 0xffffffffu;
+    for (int r = 0; r < C; ++r) {
+      const int64_t c = s_npart[2 * r];
+      const uint32_t hu = (uint32_t)s_npart[2 * r + 1];
+      if (better(c, hu, bc, bhu)) { bc = c; bhu = hu; }
+    }
     if (tid == 0) {
-      for (int i = 1; i < kWarps; ++i)
-        if (rc[i] < bc || (rc[i] == bc && (rh[i] < bh || (rh[i] == bh && ru[i] < bu)))) {
-          bc = rc[i]; bh = rh[i]; bu = ru[i];
-        }
       s_misc[MS_SINK_DIST] = bc;
-      s_misc[MS_SINK_PAR] = bc < kDInf ? bu : -1;
+      s_misc[MS_SINK_PAR] = bc < kDInf ? (int64_t)(bhu & 0xffffu) : -1;
       if (rank == 0) B->npath_reused++;
     }
     __syncthreads();
-    return s_misc[MS_SINK_DIST] < 0 ? 1 : 0;
+    return bc < 0 ? 1 : 0;
   }
 
   // Follow parents from the sink back to the anchor (every CTA does this,
@@ -874,6 +893,7 @@ struct Solver {
       B->free_top = I.ctl[CTL_FREE_TOP];
       B->cycles = B->paths = B->bf_calls = B->bf_sweeps = B->bf_max = B->moves = B->skipped = B->rows = 0;
       B->t_merge = B->t_relax = B->t_sync = B->t_gather = B->t_apply = B->t_rescan = 0;
+      B->t_rloop = B->t_rred = 0;
       B->err0 = 0;
       B->npath_reused = 0;
       B->col_rows = 0;
@@ -951,6 +971,9 @@ struct Solver {
       I.ctl[CTL_T_GATHER] += B->t_gather;
       I.ctl[CTL_T_APPLY] += B->t_apply;
       I.ctl[CTL_T_RESCAN] += B->t_rescan;
+      I.ctl[CTL_T_RLOOP] += B->t_rloop;
+      I.ctl[CTL_TSM_ON] = tsm_on ? 1 : 0;
+      I.ctl[CTL_T_RRED] += B->t_rred;
       I.ctl[CTL_NPATH_REUSED] += B->npath_reused;
       I.ctl[CTL_COL_ROWS] += B->col_rows;
       I.ctl[CTL_FRONT_SUM] += B->front_sum;
@@ -1007,20 +1030,20 @@ asral_cluster_kernel(const DevInst* __restrict__ insts, int ninst, int* work_cou
     S.c1 = min(S.k, S.c0 + S.w);
     S.wr = max(0, S.c1 - S.c0);
     const Layout L = make_layout(S.k, S.C, (int)sizeof(T));
-    S.tsm_on = 16 + L.total <= avail;   // same decision in every CTA of the cluster
+    // same decision in every CTA of the cluster
+    S.tsm_on = 16 + L.total <= avail && !(flags & OPT_NO_TC_SMEM);
     S.s_dist = reinterpret_cast<int64_t*>(base + L.dist);
     S.s_hop = reinterpret_cast<int32_t*>(base + L.hop);
     S.s_load = reinterpret_cast<int32_t*>(base + L.load);
     S.s_cap = reinterpret_cast<int32_t*>(base + L.cap);
     S.s_pen = reinterpret_cast<int32_t*>(base + L.pen);
-    S.s_front = reinterpret_cast<int32_t*>(base + L.front);
     S.s_par = reinterpret_cast<int32_t*>(base + L.par);
-    S.s_outv = reinterpret_cast<int32_t*>(base + L.outv);
-    S.s_outd = reinterpret_cast<int64_t*>(base + L.outd);
-    S.s_inv = reinterpret_cast<int32_t*>(base + L.inv);
-    S.s_ind = reinterpret_cast<int64_t*>(base + L.ind);
+    S.s_outk = reinterpret_cast<uint64_t*>(base + L.outk);
+    S.s_front = reinterpret_cast<uint64_t*>(base + L.front);
+    S.s_ink = reinterpret_cast<uint64_t*>(base + L.ink);
     S.s_incnt = reinterpret_cast<int32_t*>(base + L.incnt);
     S.s_insink = reinterpret_cast<int64_t*>(base + L.insink);
+    S.s_npart = reinterpret_cast<int64_t*>(base + L.npart);
     S.s_path = reinterpret_cast<int32_t*>(base + L.path);
     S.s_pathu = reinterpret_cast<int32_t*>(base + L.pathu);
     S.s_misc = reinterpret_cast<int64_t*>(base + L.misc);

@@ -44,6 +44,7 @@ struct lbdd_solver {
   int cluster = 0;         // 0 = auto
   int ncyc_skip = 1;
   int npath_reuse = 1;
+  int tc_smem = 1;
   int device = 0;
   int num_sms = 0;
   std::vector<void*> allocs;
@@ -216,6 +217,7 @@ extern "C" int lbdd_create(lbdd_solver** out, int32_t n, int32_t k, const void* 
   if (!out) return LBDD_ERR_ARG;
   *out = nullptr;
   if (n < 1 || k < 1 || !cm || !cap || !pen) return LBDD_ERR_ARG;
+  if (k > 65535) return LBDD_ERR_ARG;   // Bellman-Ford packs node ids in 16 bits
   if (cm_dtype != LBDD_CM_I32 && cm_dtype != LBDD_CM_I16) return LBDD_ERR_ARG;
   for (int32_t i = 0; i < k; ++i)
     if (cap[i] < 1 || pen[i] < 1) return LBDD_ERR_ARG;
@@ -284,6 +286,10 @@ extern "C" int lbdd_set_option(lbdd_solver* s, int option, int64_t value) {
       if (value != 0 && value != 1) return LBDD_ERR_ARG;
       s->ncyc_skip = (int)value;
       return LBDD_OK;
+    case LBDD_OPT_TC_SMEM:
+      if (value != 0 && value != 1) return LBDD_ERR_ARG;
+      s->tc_smem = (int)value;
+      return LBDD_OK;
     case LBDD_OPT_NPATH_REUSE:
       if (value != 0 && value != 1) return LBDD_ERR_ARG;
       s->npath_reuse = (int)value;
@@ -314,7 +320,8 @@ static int set_target(lbdd_solver* s, int64_t max_rounds, cudaStream_t st) {
 }
 
 static int solver_flags(const lbdd_solver* s) {
-  return (s->ncyc_skip ? 0 : OPT_NO_NCYC_SKIP) | (s->npath_reuse ? 0 : OPT_NO_NPATH_REUSE);
+  return (s->ncyc_skip ? 0 : OPT_NO_NCYC_SKIP) | (s->npath_reuse ? 0 : OPT_NO_NPATH_REUSE) |
+         (s->tc_smem ? 0 : OPT_NO_TC_SMEM);
 }
 
 static int choose_cluster(lbdd_solver* s) {
@@ -462,6 +469,9 @@ extern "C" int lbdd_get_stats(const lbdd_solver* s, lbdd_stats* out) {
   out->gather_ns = (int64_t)(c[CTL_T_GATHER] * ns_per_cycle);
   out->apply_ns = (int64_t)(c[CTL_T_APPLY] * ns_per_cycle);
   out->rescan_ns = (int64_t)(c[CTL_T_RESCAN] * ns_per_cycle);
+  out->relax_loop_ns = (int64_t)(c[CTL_T_RLOOP] * ns_per_cycle);
+  out->relax_reduce_ns = (int64_t)(c[CTL_T_RRED] * ns_per_cycle);
+  out->cost_slice_in_smem = c[CTL_TSM_ON];
   out->npath_reused = c[CTL_NPATH_REUSED];
   out->col_rows = c[CTL_COL_ROWS];
   out->front_sum = c[CTL_FRONT_SUM];

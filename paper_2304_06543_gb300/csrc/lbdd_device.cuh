@@ -45,6 +45,9 @@ enum CtlIndex {
   CTL_T_GATHER,
   CTL_T_APPLY,
   CTL_T_RESCAN,
+  CTL_TSM_ON,          // 1 if the last launch kept the owned cost slice in shared memory
+  CTL_T_RLOOP,         // relaxation loop only (cycles, part of CTL_T_RELAX)
+  CTL_T_RRED,          // loop + cross-warp reduction (cycles, part of CTL_T_RELAX)
   CTL_NPATH_REUSED,    // Alg. 4 answered from the converged Alg. 1 labels
   CTL_COL_ROWS,        // member rows read by column-subset rescans
   CTL_FRONT_SUM,       // sum of Bellman-Ford frontier sizes over sweeps
@@ -62,6 +65,7 @@ enum : int64_t {
 enum : int {
   OPT_NO_NCYC_SKIP = 1,   // always run the NegCycle Bellman-Ford
   OPT_NO_NPATH_REUSE = 2, // always run the NegPath Bellman-Ford
+  OPT_NO_TC_SMEM = 4,     // keep the owned cost slice in global memory only
 };
 
 // Device view of one instance.  Pointers are device memory owned by the
