@@ -18,13 +18,15 @@
 //   4. unpack to the (tc, td) int32 pair.
 // Step 3 reads every CM byte of the allotted rows exactly once and is the
 // HBM-bound kernel; everything else moves O(n + k*k) bytes.
+#include <algorithm>
+
 #include "lbdd_device.cuh"
 
 namespace lbdd {
 
 constexpr int kTile = kThreads * 8;     // radix-sort tile (elements)
 constexpr int kChunk = 512;             // rows per scan work item
-constexpr int kScanUnroll = 8;          // rows in flight per thread
+constexpr int kScanUnroll = 6;          // rows in flight per thread (plus ids of the next 6)
 
 struct BtWorkspace {
   int32_t *k0, *v0, *k1, *v1;   // radix ping-pong
@@ -33,6 +35,8 @@ struct BtWorkspace {
   int32_t* seg_end;             // k
   int32_t* item_off;            // k + 1
   unsigned long long* t64;      // k x k packed (cost + 2^31) << 32 | d
+  int4* items;                  // explicit work items {center, first row, rows, 0}
+  int* err;                     // [0] unused, [1] the work-item queue counter
   int64_t ntiles;
   size_t bytes;
 };
@@ -57,6 +61,8 @@ static BtWorkspace carve(void* base, int32_t n, int32_t k) {
   W.seg_end = reinterpret_cast<int32_t*>(take(4ull * k));
   W.item_off = reinterpret_cast<int32_t*>(take(4ull * (k + 1)));
   W.t64 = reinterpret_cast<unsigned long long*>(take(8ull * k * k));
+  W.items = reinterpret_cast<int4*>(take(16ull * ((size_t)n / kChunk + (size_t)k + 1)));
+  W.err = reinterpret_cast<int*>(take(16));   // err, then the item queue counter
   W.bytes = o;
   return W;
 }
@@ -186,49 +192,69 @@ __global__ void __launch_bounds__(kThreads) bt_items(const int32_t* __restrict__
     t64[i] = ~0ull;
 }
 
+// Explicit item list: item_off[c] + i -> {c, first row, rows}.
+__global__ void __launch_bounds__(kThreads) bt_item_list(const int32_t* __restrict__ seg_start,
+                                                         const int32_t* __restrict__ seg_end,
+                                                         const int32_t* __restrict__ item_off,
+                                                         int32_t k, int4* items) {
+  for (int64_t c = blockIdx.x * (int64_t)kThreads + threadIdx.x; c < k;
+       c += (int64_t)gridDim.x * kThreads) {
+    const int32_t s0 = seg_start[c], s1 = seg_end[c];
+    int32_t it = item_off[c];
+    for (int32_t r = s0; r < s1; r += kChunk, ++it) items[it] = make_int4((int)c, r, min(kChunk, s1 - r), 0);
+  }
+}
+
 // ------------------------------------------------------------------ scan ---
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1)
 bt_scan_rows(const T* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
-             const int32_t* __restrict__ perm,
-             const int32_t* __restrict__ seg_start, const int32_t* __restrict__ seg_end,
-             const int32_t* __restrict__ item_off, unsigned long long* t64) {
+             const int32_t* __restrict__ perm, const int32_t* __restrict__ item_off,
+             const int4* __restrict__ items, unsigned long long* t64, int* work) {
   constexpr int VPL = 16 / (int)sizeof(T);
+  constexpr int U = kScanUnroll;
   __shared__ int2 red[kThreads * VPL];
+  __shared__ int s_item[2];
   const int S = (k + VPL - 1) / VPL;       // 16-byte column groups per row
   const int R = kThreads / S;              // row groups
   const int tid = threadIdx.x, slot = tid % S, g = tid / S;
   const int32_t total = item_off[k];
-  for (int32_t item = blockIdx.x; item < total; item += gridDim.x) {
-    // center owning this item: last c with item_off[c] <= item
-    int lo = 0, hi = k;
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (item_off[mid] <= item) lo = mid; else hi = mid;
-    }
-    const int32_t c = lo;
-    const int32_t r0 = seg_start[c] + (item - item_off[c]) * kChunk;
-    const int32_t r1 = min(seg_end[c], r0 + kChunk);
+  // items come from a global queue: CTAs that finish early take more
+  if (tid == 0) s_item[0] = atomicAdd(work, 1);
+  __syncthreads();
+  for (int32_t item = s_item[0];;) {
+    if (item >= total) break;
+    const int4 desc = items[item];
+    // fetch the next item now; it is read after the reduction's barrier
+    if (tid == 0) s_item[1] = atomicAdd(work, 1);
+    const int32_t c = desc.x, r0 = desc.y, r1 = desc.y + desc.z;
     int32_t bt[VPL], bd[VPL];
 #pragma unroll
     for (int q = 0; q < VPL; ++q) { bt[q] = kTInf; bd[q] = -1; }
     if (g < R) {
-      // kScanUnroll rows per step: their unit ids first, then all 16-byte row
-      // loads, so that many independent loads are in flight per thread.
-      // Rows of a thread arrive in increasing d: a strict '<' keeps the
-      // lowest d among equal costs.
-      for (int32_t p = r0 + g; p < r1; p += kScanUnroll * R) {
-        int32_t d[kScanUnroll];
+      // software pipeline: the unit ids of the next U rows are loaded while
+      // the current U rows are loaded and reduced.  Rows of a thread arrive
+      // in increasing d, so a strict '<' keeps the lowest d on equal cost.
+      int32_t dn[U];
 #pragma unroll
-        for (int u = 0; u < kScanUnroll; ++u) {
-          const int32_t pu = p + u * R;
-          d[u] = pu < r1 ? (int32_t)min((uint32_t)__ldg(perm + pu), (uint32_t)(n - 1)) : -1;
+      for (int u = 0; u < U; ++u) {
+        const int32_t pu = r0 + g + u * R;
+        dn[u] = pu < r1 ? (int32_t)min((uint32_t)__ldg(perm + pu), (uint32_t)(n - 1)) : -1;
+      }
+      for (int32_t p = r0 + g; p < r1; p += U * R) {
+        int32_t d[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) d[u] = dn[u];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int32_t pu = p + (U + u) * R;
+          dn[u] = pu < r1 ? (int32_t)min((uint32_t)__ldg(perm + pu), (uint32_t)(n - 1)) : -1;
         }
-        int32_t own[kScanUnroll];
-        Vec16<T> x[kScanUnroll];
+        int32_t own[U];
+        Vec16<T> x[U];
 #pragma unroll
-        for (int u = 0; u < kScanUnroll; ++u) {
+        for (int u = 0; u < U; ++u) {
           if (d[u] >= 0) {
             const T* rp = cm + (int64_t)d[u] * ld;
             own[u] = (int32_t)rp[c];
@@ -236,7 +262,7 @@ bt_scan_rows(const T* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
           }
         }
 #pragma unroll
-        for (int u = 0; u < kScanUnroll; ++u) {
+        for (int u = 0; u < U; ++u) {
           if (d[u] < 0) continue;
 #pragma unroll
           for (int q = 0; q < VPL; ++q) {
@@ -250,27 +276,34 @@ bt_scan_rows(const T* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
     }
     __syncthreads();
     for (int col = tid; col < k; col += kThreads) {
-      int32_t t = kTInf, d = -1;
+      int32_t t = kTInf, dd = -1;
       for (int gg = 0; gg < R; ++gg) {
         const int2 e = red[gg * S * VPL + col];
-        if (lex_less(e.x, e.y, t, d)) { t = e.x; d = e.y; }
+        if (lex_less(e.x, e.y, t, dd)) { t = e.x; dd = e.y; }
       }
-      if (d >= 0 && col != c) {
+      if (dd >= 0 && col != c) {
         const unsigned long long key =
-            ((unsigned long long)(uint32_t)(t + (int64_t)2147483648LL) << 32) | (uint32_t)d;
+            ((unsigned long long)(uint32_t)(t + (int64_t)2147483648LL) << 32) | (uint32_t)dd;
         atomicMin(&t64[(int64_t)c * k + col], key);
       }
     }
+    item = s_item[1];
     __syncthreads();
+    if (tid == 0) s_item[0] = item;   // keep s_item[1] free for the next fetch
   }
 }
 
 __global__ void __launch_bounds__(kThreads) bt_unpack(const unsigned long long* __restrict__ t64,
-                                                      int32_t k, int32_t* tc, int32_t* td) {
+                                                      int32_t k, int32_t* tc, int32_t* td,
+                                                      const int* err) {
+  const bool bad = *err != 0;   // reserved error flag: marks the whole table
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < (int64_t)k * k;
        i += (int64_t)gridDim.x * kThreads) {
     const unsigned long long e = t64[i];
-    if (e == ~0ull) {
+    if (bad) {
+      tc[i] = kTInf;
+      td[i] = -2;
+    } else if (e == ~0ull) {
       tc[i] = kTInf;
       td[i] = -1;
     } else {
@@ -308,13 +341,16 @@ cudaError_t best_transfer_run(int32_t n, int32_t k, const void* cm, int elem_byt
   bt_items<<<grid_lin, kThreads, 0, st>>>(W.seg_start, W.seg_end, k, W.item_off, W.t64);
   bt_scan<<<1, kThreads, 0, st>>>(W.item_off, k, W.item_off + k);
   const int grid_scan = num_sms;
-  if (elem_bytes == 2)
+  cudaMemsetAsync(W.err, 0, 2 * sizeof(int), st);
+  bt_item_list<<<grid_lin, kThreads, 0, st>>>(W.seg_start, W.seg_end, W.item_off, k, W.items);
+  if (elem_bytes == 2) {
     bt_scan_rows<int16_t><<<grid_scan, kThreads, 0, st>>>(
-        static_cast<const int16_t*>(cm), ld, n, k, sv, W.seg_start, W.seg_end, W.item_off, W.t64);
-  else
+        static_cast<const int16_t*>(cm), ld, n, k, sv, W.item_off, W.items, W.t64, W.err + 1);
+  } else {
     bt_scan_rows<int32_t><<<grid_scan, kThreads, 0, st>>>(
-        static_cast<const int32_t*>(cm), ld, n, k, sv, W.seg_start, W.seg_end, W.item_off, W.t64);
-  bt_unpack<<<grid_lin, kThreads, 0, st>>>(W.t64, k, tc, td);
+        static_cast<const int32_t*>(cm), ld, n, k, sv, W.item_off, W.items, W.t64, W.err + 1);
+  }
+  bt_unpack<<<grid_lin, kThreads, 0, st>>>(W.t64, k, tc, td, W.err);
   return cudaGetLastError();
 }
 
