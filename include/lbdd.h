@@ -135,15 +135,108 @@ int lbdd_solve(lbdd_solver* s, int64_t max_rounds);
  * Stream-ordered; no host synchronisation. */
 int lbdd_reset(lbdd_solver* s);
 
-/* Solve m solvers' instances together in one persistent launch: each
- * thread-block cluster takes the next unsolved instance (largest n*k first).
- * Every solver must have been created on the same device.  max_rounds as in
- * lbdd_solve, applied to each instance.  cluster_size 1..16 (0 = auto);
- * max_clusters 0 = as many as fit on the GPU.  Work is issued on `stream`
- * (NULL = legacy default stream) and synchronised before returning.
- * Returns the first failing instance's status. */
+/* ---------------------------------------------------------------------
+ * Batched solves.  Every instance is an independent run of Alg. 2 (the
+ * paper solves one instance at a time; batching many is this library's
+ * addition), so a batch is a scheduling problem only: which cluster size
+ * each instance gets and how the SMs are shared.
+ *
+ * lbdd_batch_create plans a batch of m solvers (all created on the current
+ * device; they stay owned by the caller and must outlive the batch):
+ *   - each instance gets a thread-block cluster of C CTAs (1, 2, 4, 8, 16),
+ *     from the per-device table that lbdd_autotune measures (the SM-time per
+ *     round, least first; instances that would outlast the rest of the
+ *     batch move to faster clusters); without measurements about k/128
+ *     CTAs; cluster_size > 0 forces one size for all;
+ *   - instances with the same cost width and C form a group: one persistent
+ *     launch whose clusters take instances from a device-side queue, the
+ *     longest estimated solve first; the SMs are shared between the groups
+ *     in proportion to their estimated SM-time (max_clusters > 0 caps each
+ *     group's clusters) and the groups run concurrently;
+ *   - one pass (set the round targets, the concurrent group launches, read
+ *     the statuses) is captured once as a CUDA graph.
+ * lbdd_batch_run replays the graph on `stream` (given at create) and waits:
+ * every instance advances by up to max_rounds rounds (< 0: to completion),
+ * exactly as lbdd_solve(s, max_rounds) would advance it alone.  Returns the
+ * first failing instance's status.
+ * lbdd_batch_plan reports the plan: cluster_of[m] (nullable), the number of
+ * groups, and per group (up to max_groups) its cluster size, cluster count
+ * and instance count (each nullable).
+ * lbdd_solve_batch is create + run + destroy without the graph. */
+typedef struct lbdd_batch lbdd_batch;
+int lbdd_batch_create(lbdd_batch** out, lbdd_solver* const* solvers, int m, int cluster_size,
+                      int max_clusters, void* stream);
+int lbdd_batch_run(lbdd_batch* b, int64_t max_rounds);
+int lbdd_batch_plan(const lbdd_batch* b, int32_t* cluster_of, int32_t* ngroups,
+                    int32_t* group_cluster, int32_t* group_clusters, int32_t* group_size,
+                    int max_groups);
+void lbdd_batch_destroy(lbdd_batch* b);
 int lbdd_solve_batch(lbdd_solver* const* solvers, int m, int64_t max_rounds,
                      int cluster_size, int max_clusters, void* stream);
+
+/* Autotuner of the batch plan: for every (cost width, k bucket
+ * 2^(b-1) < k <= 2^b) present among the m solvers, clones the instance with
+ * the most units and times probe_rounds rounds (after the prologue) on one
+ * cluster of each size that fits; the ns per round are kept per device for
+ * the process's lifetime and used by every later batch plan and server pass.
+ * The solvers themselves are not modified.  lbdd_tune_get reads one entry
+ * (0 = not measured); lbdd_tune_clear forgets all. */
+int lbdd_autotune(lbdd_solver* const* solvers, int m, int probe_rounds, void* stream);
+int lbdd_tune_get(int cm_dtype, int32_t k, int cluster_size, double* ns_per_round);
+int lbdd_tune_clear(void);
+
+/* ---------------------------------------------------------------------
+ * Request server (continuous batching; no counterpart in the paper).
+ * Solve requests of mixed sizes are admitted in arrival order while the
+ * device-memory budget and the active-slot limit allow; admitted requests
+ * keep CM, allotment and loads resident on the device and advance together
+ * in time-sliced passes (the batch plan above, shortest remaining work
+ * first, each pass ending after quantum_us); requests admitted during a
+ * pass join the next one, finished ones are retired (allotment copied to the
+ * caller's buffer, device memory freed) while others keep solving.  Each
+ * result is bit-identical to the same instance solved alone. */
+typedef struct lbdd_server lbdd_server;
+typedef struct lbdd_server_config {
+  size_t budget_bytes;   /* device bytes all admitted requests may hold */
+  int max_active;        /* requests admitted at once (0 = one per SM) */
+  int64_t quantum_us;    /* pass length in microseconds (0 = 20000) */
+  int cluster_size;      /* 0 = from the batch plan, else forced (1..16) */
+} lbdd_server_config;
+typedef enum lbdd_request_state {
+  LBDD_REQ_QUEUED = 0, LBDD_REQ_ACTIVE = 1, LBDD_REQ_DONE = 2, LBDD_REQ_FAILED = 3
+} lbdd_request_state;
+typedef struct lbdd_request_info {
+  int32_t state;         /* lbdd_request_state */
+  int32_t status;        /* LBDD_OK, or why the request failed */
+  int64_t objective;     /* Eq. (1) of the final allotment (state DONE) */
+  int64_t rounds;        /* rounds done at the end of the last pass */
+  int64_t submit_ns, admit_ns, done_ns;  /* server clock (ns since create); -1 = not yet */
+} lbdd_request_info;
+typedef struct lbdd_server_stats {
+  int64_t passes, admitted, completed, failed, queued;
+  int64_t bytes_in_use, peak_bytes;      /* budget held now / at most */
+  int64_t busy_ns, uptime_ns;            /* time with a pass in flight / since create */
+  int64_t peak_active;                   /* most requests in one pass */
+} lbdd_server_stats;
+/* The server runs on the current device with its own streams and threads. */
+int lbdd_server_create(lbdd_server** out, const lbdd_server_config* cfg);
+/* Queue one request.  cm (host, n*k demand-major, cm_dtype) and assign_out
+ * (host int32[n]) must stay valid until the request is DONE or FAILED;
+ * cap and pen are copied.  *ticket identifies the request.  A request whose
+ * footprint exceeds the whole budget fails with LBDD_ERR_BUDGET. */
+int lbdd_server_submit(lbdd_server* srv, int32_t n, int32_t k, const void* cm, int cm_dtype,
+                       const int32_t* cap, const int32_t* pen, int32_t* assign_out,
+                       int64_t* ticket);
+/* Wait up to timeout_ms (< 0: forever, 0: do not wait) for a request to end;
+ * fills *out either way.  LBDD_OK when it ended, LBDD_ERR_TIMEOUT if not. */
+int lbdd_server_poll(lbdd_server* srv, int64_t ticket, int64_t timeout_ms,
+                     lbdd_request_info* out);
+/* Forget an ended request's record (its ticket becomes invalid). */
+int lbdd_server_release(lbdd_server* srv, int64_t ticket);
+int lbdd_server_get_stats(lbdd_server* srv, lbdd_server_stats* out);
+/* Stop: queued requests fail with LBDD_ERR_STATE, the pass in flight ends
+ * at its quantum, everything is freed. */
+void lbdd_server_destroy(lbdd_server* srv);
 
 /* Tracked objective Delta of Alg. 2 (equals Eq. (1) of the current
  * allotment).  out: host pointer. */
@@ -156,7 +249,6 @@ int lbdd_assignment(const lbdd_solver* s, int32_t* out, int out_is_device);
 /* Copy the k center loads (int32, host). */
 int lbdd_loads(const lbdd_solver* s, int32_t* out);
 
-/* Rounds completed so far (host int64). */
 int lbdd_rounds_done(const lbdd_solver* s, int64_t* out);
 
 /* Counters of the solve so far (host struct). */

@@ -139,15 +139,48 @@ BATCH_SEED0 = 1000      # batched mix: instance i uses seed 1000 + i
 SERVE_SEED0 = 100000    # serving stream: request i uses seed 100000 + i
 
 
-def batch_recipe(i: int, n_range=(3.0, 5.0), k_range=(1.0, 2.6020599913279625)) -> Recipe:
-    """Instance i of the batched mix: n log-uniform in [10^3, 10^5), k
-    log-uniform in [10, 400), otherwise generated like "tiny"."""
+def _mix_recipe(seed: int, name: str, n_range, k_range) -> Recipe:
     lib = _load()
-    seed = BATCH_SEED0 + i
     n = int(lib.lbdd_gen_logu_size(seed, 0, n_range[0], n_range[1]))
     k = int(lib.lbdd_gen_logu_size(seed, 1, k_range[0], k_range[1]))
     return Recipe(n=n, k=k, seed=seed, layout="uniform", scale=100.0, cap_frac=0.9,
-                  cap_dist="uniform", pen=(50, 500), name=f"batch{i}")
+                  cap_dist="uniform", pen=(50, 500), name=name)
+
+
+def batch_recipe(i: int, n_range=(3.0, 5.0), k_range=(1.0, 2.6020599913279625)) -> Recipe:
+    """Instance i of the batched mix: n log-uniform in [10^3, 10^5), k
+    log-uniform in [10, 400), otherwise generated like "tiny"."""
+    return _mix_recipe(BATCH_SEED0 + i, f"batch{i}", n_range, k_range)
+
+
+SERVE_LARGE = (1_000_000, 1000)   # size of the serving stream's large requests
+
+
+def serve_recipe(i: int, large_frac: float = 0.05, large=SERVE_LARGE):
+    """Request i of the serving stream and whether it is a large one.
+
+    With probability large_frac (one draw of the counter stream of seed
+    100000 + i) the request is large: n x k = `large`, clustered demand,
+    road factors and Zipf capacities like the city-scale instance.  Otherwise
+    it is sized and generated like the batched mix."""
+    lib = _load()
+    seed = SERVE_SEED0 + i
+    if lib.lbdd_gen_u01(seed, 40, 0) < large_frac:
+        n, k = large
+        return Recipe(n=int(n), k=int(k), seed=seed, layout="gmm", scale=1000.0, road=(1.0, 1.5),
+                      cap_frac=0.85, cap_dist="zipf", zipf=1.2, pen=(100, 5000),
+                      name=f"serve{i}L"), True
+    return _mix_recipe(seed, f"serve{i}", (3.0, 5.0), (1.0, 2.6020599913279625)), False
+
+
+def arrival_times(count: int, rate: float) -> np.ndarray:
+    """Poisson arrivals of the serving stream (seconds from the first):
+    exponential gaps -ln(1 - U) / rate, U from the counter stream of seed
+    100000; arrival 0 is at time 0."""
+    lib = _load()
+    gaps = np.array([-np.log1p(-lib.lbdd_gen_u01(SERVE_SEED0, 41, i)) for i in range(count)])
+    gaps[0] = 0.0
+    return np.cumsum(gaps) / rate
 
 
 def make(recipe: Recipe, dtype: str = "i32", points_only: bool = False) -> Instance:

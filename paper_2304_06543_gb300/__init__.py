@@ -22,6 +22,7 @@ __all__ = [
     "load", "LbddError", "Solver", "create", "solve", "reset", "solve_batch", "objective",
     "assignment", "loads", "rounds_done", "get_stats", "best_transfer_table",
     "best_transfer", "best_transfer_workspace", "cm_pitch", "strerror", "destroy",
+    "Batch", "autotune", "tune_get", "tune_clear", "Server", "RequestInfo", "ServerStats",
 ]
 
 OK = 0
@@ -53,6 +54,26 @@ _STAT_FIELDS = (
 
 class _Stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in _STAT_FIELDS] + [("front_hist", ctypes.c_int64 * 6)]
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int),
+                ("quantum_us", ctypes.c_int64), ("cluster_size", ctypes.c_int)]
+
+
+class _RequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("objective", ctypes.c_int64), ("rounds", ctypes.c_int64),
+                ("submit_ns", ctypes.c_int64), ("admit_ns", ctypes.c_int64),
+                ("done_ns", ctypes.c_int64)]
+
+
+_SERVER_STAT_FIELDS = ("passes", "admitted", "completed", "failed", "queued", "bytes_in_use",
+                       "peak_bytes", "busy_ns", "uptime_ns", "peak_active")
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in _SERVER_STAT_FIELDS]
 
 
 def load():
@@ -87,6 +108,23 @@ def load():
         lib.lbdd_cm_pitch.restype = i64
         lib.lbdd_solver_cm.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(c_int),
                                        ctypes.POINTER(i64)]
+        PI32 = ctypes.POINTER(i32)
+        lib.lbdd_batch_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(P), c_int, c_int,
+                                          c_int, P]
+        lib.lbdd_batch_run.argtypes = [P, i64]
+        lib.lbdd_batch_plan.argtypes = [P, PI32, PI32, PI32, PI32, PI32, c_int]
+        lib.lbdd_batch_destroy.argtypes = [P]
+        lib.lbdd_batch_destroy.restype = None
+        lib.lbdd_autotune.argtypes = [ctypes.POINTER(P), c_int, c_int, P]
+        lib.lbdd_tune_get.argtypes = [c_int, i32, c_int, ctypes.POINTER(ctypes.c_double)]
+        lib.lbdd_tune_clear.argtypes = []
+        lib.lbdd_server_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(_ServerConfig)]
+        lib.lbdd_server_submit.argtypes = [P, i32, i32, P, c_int, P, P, P, ctypes.POINTER(i64)]
+        lib.lbdd_server_poll.argtypes = [P, i64, i64, ctypes.POINTER(_RequestInfo)]
+        lib.lbdd_server_release.argtypes = [P, i64]
+        lib.lbdd_server_get_stats.argtypes = [P, ctypes.POINTER(_ServerStats)]
+        lib.lbdd_server_destroy.argtypes = [P]
+        lib.lbdd_server_destroy.restype = None
         _lib = lib
     return _lib
 
@@ -186,7 +224,7 @@ def reset(h):
 
 def solve_batch(handles, max_rounds: int = -1, cluster_size: int = 0, max_clusters: int = 0,
                 stream=None):
-    arr = (ctypes.c_void_p * len(handles))(*[h.value if hasattr(h, "value") else h for h in handles])
+    arr = _handles(handles)
     _check(load().lbdd_solve_batch(arr, len(handles), int(max_rounds), cluster_size, max_clusters,
                                    _stream_handle(stream)), "lbdd_solve_batch")
 
@@ -314,6 +352,164 @@ class Solver:
         if self.h is not None:
             destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _handles(handles):
+    return (ctypes.c_void_p * len(handles))(
+        *[h.h.value if isinstance(h, Solver) else (h.value if hasattr(h, "value") else h)
+          for h in handles])
+
+
+class Batch:
+    """lbdd_batch: a planned, graph-captured batch of solvers (Solver objects
+    or handles, which must outlive the batch)."""
+
+    def __init__(self, solvers, cluster_size: int = 0, max_clusters: int = 0, stream=None):
+        self.m = len(solvers)
+        self._keep = list(solvers)
+        h = ctypes.c_void_p()
+        _check(load().lbdd_batch_create(ctypes.byref(h), _handles(solvers), self.m, cluster_size,
+                                        max_clusters, _stream_handle(stream)),
+               "lbdd_batch_create")
+        self.h = h
+
+    def run(self, max_rounds: int = -1):
+        _check(load().lbdd_batch_run(self.h, int(max_rounds)), "lbdd_batch_run")
+
+    def plan(self):
+        """(cluster size per instance, [(cluster size, clusters, instances) per group])."""
+        m = self.m
+        cl = (ctypes.c_int32 * m)()
+        ng = ctypes.c_int32()
+        gc, gn, gs = (ctypes.c_int32 * 16)(), (ctypes.c_int32 * 16)(), (ctypes.c_int32 * 16)()
+        _check(load().lbdd_batch_plan(self.h, cl, ctypes.byref(ng), gc, gn, gs, 16),
+               "lbdd_batch_plan")
+        return list(cl), [(gc[g], gn[g], gs[g]) for g in range(ng.value)]
+
+    def close(self):
+        if self.h is not None:
+            load().lbdd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(solvers, probe_rounds: int = 256, stream=None):
+    _check(load().lbdd_autotune(_handles(solvers), len(solvers), int(probe_rounds),
+                                _stream_handle(stream)), "lbdd_autotune")
+
+
+def tune_get(cm_dtype: int, k: int, cluster_size: int) -> float:
+    v = ctypes.c_double()
+    _check(load().lbdd_tune_get(cm_dtype, int(k), int(cluster_size), ctypes.byref(v)),
+           "lbdd_tune_get")
+    return v.value
+
+
+def tune_clear():
+    _check(load().lbdd_tune_clear(), "lbdd_tune_clear")
+
+
+REQ_QUEUED, REQ_ACTIVE, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
+
+@dataclass
+class RequestInfo:
+    state: int
+    status: int
+    objective: int
+    rounds: int
+    submit_ns: int
+    admit_ns: int
+    done_ns: int
+
+
+@dataclass
+class ServerStats:
+    passes: int
+    admitted: int
+    completed: int
+    failed: int
+    queued: int
+    bytes_in_use: int
+    peak_bytes: int
+    busy_ns: int
+    uptime_ns: int
+    peak_active: int
+
+
+class Server:
+    """lbdd_server: continuous-batching request server on the current device.
+
+    submit() keeps references to the request's host arrays until the request
+    is released (``result``/``release``)."""
+
+    def __init__(self, budget_bytes: int, max_active: int = 0, quantum_us: int = 0,
+                 cluster_size: int = 0):
+        cfg = _ServerConfig(int(budget_bytes), int(max_active), int(quantum_us), int(cluster_size))
+        h = ctypes.c_void_p()
+        _check(load().lbdd_server_create(ctypes.byref(h), ctypes.byref(cfg)), "lbdd_server_create")
+        self.h = h
+        self._bufs = {}
+
+    def submit(self, cm: np.ndarray, cap, pen) -> int:
+        cm = np.ascontiguousarray(cm)
+        dt = {np.dtype(np.int32): CM_I32, np.dtype(np.int16): CM_I16}[cm.dtype]
+        n, k = cm.shape
+        cap = np.ascontiguousarray(cap, dtype=np.int32)
+        pen = np.ascontiguousarray(pen, dtype=np.int32)
+        out = np.empty(n, np.int32)
+        t = ctypes.c_int64()
+        _check(load().lbdd_server_submit(self.h, int(n), int(k), cm.ctypes.data, dt,
+                                         cap.ctypes.data, pen.ctypes.data, out.ctypes.data,
+                                         ctypes.byref(t)), "lbdd_server_submit")
+        self._bufs[t.value] = (cm, out)
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """RequestInfo, or None if the request has not ended within timeout_ms."""
+        info = _RequestInfo()
+        rc = load().lbdd_server_poll(self.h, int(ticket), int(timeout_ms), ctypes.byref(info))
+        if rc == ERR_TIMEOUT:
+            return None
+        _check(rc, "lbdd_server_poll")
+        return RequestInfo(*[getattr(info, f) for f, _ in _RequestInfo._fields_])
+
+    def result(self, ticket: int, timeout_ms: int = -1):
+        """(RequestInfo, allotment) once the request ended; releases it."""
+        info = self.poll(ticket, timeout_ms)
+        if info is None:
+            return None
+        _, out = self._bufs.pop(ticket)
+        _check(load().lbdd_server_release(self.h, int(ticket)), "lbdd_server_release")
+        return info, out
+
+    def stats(self) -> ServerStats:
+        s = _ServerStats()
+        _check(load().lbdd_server_get_stats(self.h, ctypes.byref(s)), "lbdd_server_get_stats")
+        return ServerStats(*[getattr(s, f) for f in _SERVER_STAT_FIELDS])
+
+    def close(self):
+        if self.h is not None:
+            load().lbdd_server_destroy(self.h)
+            self.h = None
+            self._bufs.clear()
 
     def __del__(self):
         try:

@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbdd.so")
 
-SOURCES = ["asral_solver.cu", "best_transfer.cu", "lbdd_api.cu", "best_transfer_noalloc.cu"]
+SOURCES = ["asral_solver.cu", "best_transfer.cu", "lbdd_api.cu", "best_transfer_noalloc.cu",
+           "lbdd_batch.cu", "lbdd_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -26,6 +26,7 @@
 // Tie-breaking is canonical and identical to the CPU oracle: (cost, unit)
 // lexicographic in T, lowest predecessor index on equal Bellman-Ford labels.
 #include <limits>
+#include <mutex>
 
 #include "lbdd_device.cuh"
 
@@ -86,7 +87,11 @@ __host__ __device__ inline Layout make_layout(int32_t k, int32_t C, int32_t elem
 enum { SK_CHANGED = 0, SK_DIST, SK_PAR };
 // Slots of the per-CTA scalar block.
 enum { MS_SINK_DIST = 0, MS_SINK_PAR, MS_LCNT0, MS_LCNT1, MS_PATHLEN, MS_OWN_SINK_CHG0,
-       MS_OWN_SINK_CHG1, MS_OWN_SINK_DIST, MS_OWN_SINK_PAR, MS_NAFF, MS_MERGE_ANY };
+       MS_OWN_SINK_CHG1, MS_OWN_SINK_DIST, MS_OWN_SINK_PAR, MS_NAFF, MS_MERGE_ANY, MS_STOP0,
+       MS_STOP1 };
+
+// Rounds between two checks of the launch's time quantum.
+constexpr int kQuantumCheck = 8;
 
 // Counters and timers kept by thread 0 of CTA 0 (shared memory, so that
 // they cost no registers in the other threads).
@@ -95,6 +100,7 @@ struct Book {
   int64_t t_merge, t_relax, t_sync, t_gather, t_apply, t_rescan, t_rloop, t_rred;
   int64_t npath_reused, col_rows, front_sum, front_hist[6];
   int64_t err0;   // a guard tripped (corrupt state; never expected)
+  uint64_t deadline;   // globaltimer ns at which the launch yields (0: never)
 };
 
 template <typename T>
@@ -110,6 +116,7 @@ struct Solver {
   int32_t n, k, C, rank, w, ws, c0, c1, wr;
   int tid;
   int flags;
+  bool quantum_on;    // the launch is time-sliced (Book::deadline set)
   bool tsm_on;        // owned cost slice resident in shared memory
   int64_t* s_dist;    // labels of the owned columns (and 0 at the source)
   int32_t* s_hop;     // sweep of each owned column's last label change
@@ -905,7 +912,18 @@ struct Solver {
     const bool allow_skip = !(flags & OPT_NO_NCYC_SKIP);
     int64_t status = ST_OK;
     int64_t r = r_begin;
+    int nchk = 0;
     for (; r < r_end; ++r) {
+      // Time-sliced launches yield between rounds once the quantum is spent.
+      // CTA 0 decides; the flag alternates between two slots, so a slot is
+      // rewritten only after the barrier that follows every CTA's read of it.
+      if (quantum_on && r > r_begin && (r - r_begin) % kQuantumCheck == 0) {
+        const int slot = MS_STOP0 + (nchk & 1);
+        ++nchk;
+        if (rank == 0 && tid == 0) s_misc[slot] = gtimer_ns() >= B->deadline ? 1 : 0;
+        cluster_sync_all();
+        if (dsmem_ld64(dsmem_addr(&s_misc[slot], 0)) != 0) break;
+      }
       // Alg. 2 (extract-min, allot, objective update): next unit of the MinDistance order goes
       // to its most suitable center; pay the penalty if it had no vacancy.
       const uint64_t tm0 = timer() ? clock_cycles() : 0;
@@ -998,7 +1016,8 @@ struct Solver {
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1)
-asral_cluster_kernel(const DevInst* __restrict__ insts, int ninst, int* work_counter, int flags) {
+asral_cluster_kernel(const DevInst* __restrict__ insts, int ninst, int* work_counter, int flags,
+                     uint64_t quantum_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ DevInst s_inst;
   __shared__ Book s_book;
@@ -1009,11 +1028,29 @@ asral_cluster_kernel(const DevInst* __restrict__ insts, int ninst, int* work_cou
   S.C = (int)cluster_nrank();
   S.flags = flags;
   S.buf = 0;
+  S.quantum_on = quantum_ns != 0;
+  if (S.rank == 0 && S.tid == 0) s_book.deadline = S.quantum_on ? gtimer_ns() + quantum_ns : 0;
   int64_t* s_item = reinterpret_cast<int64_t*>(smem);   // first 16 bytes: work item
   unsigned char* base = smem + 16;
   const uint32_t avail = dyn_smem_bytes();
   for (;;) {
-    if (S.rank == 0 && S.tid == 0) s_item[0] = atomicAdd(work_counter, 1);
+    if (S.rank == 0 && S.tid == 0) {
+      // Next instance with rounds left and no error; none once the quantum
+      // is spent.  Only this thread decides, so the cluster agrees.
+      int it = ninst;
+      if (!S.quantum_on || gtimer_ns() < s_book.deadline) {
+        for (;;) {
+          it = atomicAdd(work_counter, 1);
+          if (it >= ninst) break;
+          const int64_t* c = insts[it].ctl;
+          const int64_t target = min((int64_t)insts[it].n, __ldcg(c + CTL_TARGET));
+          if (__ldcg(c + CTL_STATUS) == 0 &&
+              (__ldcg(c + CTL_PROLOGUE) == 0 || __ldcg(c + CTL_ROUNDS) < target))
+            break;
+        }
+      }
+      s_item[0] = it;
+    }
     __syncthreads();
     cluster_sync_all();
     const int item = (int)dsmem_ld64(dsmem_addr(s_item, 0));
@@ -1080,14 +1117,15 @@ int solver_max_k(int C, int elem_bytes) {
 }
 
 template <typename T>
+cudaError_t prepare_solver_t(int C, size_t smem);
+
+template <typename T>
 cudaError_t launch_solver_t(const DevInst* d_insts, int ninst, int* d_counter, int C,
-                            int nclusters, size_t smem, int flags, cudaStream_t st) {
+                            int nclusters, size_t smem, int flags, cudaStream_t st,
+                            uint64_t quantum_ns, bool set_attrs) {
   auto kern = asral_cluster_kernel<T>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  if (C > 8) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (set_attrs) {
+    const cudaError_t e = prepare_solver_t<T>(C, smem);
     if (e != cudaSuccess) return e;
   }
   cudaLaunchConfig_t cfg = {};
@@ -1102,15 +1140,45 @@ cudaError_t launch_solver_t(const DevInst* d_insts, int ninst, int* d_counter, i
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, d_insts, ninst, d_counter, flags);
+  return cudaLaunchKernelEx(&cfg, kern, d_insts, ninst, d_counter, flags, quantum_ns);
+}
+
+// Kernel attributes only ever grow (a launch needs at least its own dynamic
+// shared memory; concurrent callers must not lower what another one set).
+template <typename T>
+cudaError_t prepare_solver_t(int C, size_t smem) {
+  static std::mutex mu;
+  static size_t cur_smem = 0;
+  static bool non_portable = false;
+  std::lock_guard<std::mutex> lk(mu);
+  auto kern = asral_cluster_kernel<T>;
+  if (smem > cur_smem) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cur_smem = smem;
+  }
+  if (C > 8 && !non_portable) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    non_portable = true;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t prepare_solver(int C, int elem_bytes, size_t smem) {
+  return elem_bytes == 2 ? prepare_solver_t<int16_t>(C, smem) : prepare_solver_t<int32_t>(C, smem);
 }
 
 cudaError_t launch_solver(const DevInst* d_insts, int ninst, int* d_counter, int C,
                           int nclusters, int elem_bytes, size_t smem, int flags,
-                          cudaStream_t st) {
+                          cudaStream_t st, uint64_t quantum_ns, bool set_attrs) {
   if (elem_bytes == 2)
-    return launch_solver_t<int16_t>(d_insts, ninst, d_counter, C, nclusters, smem, flags, st);
-  return launch_solver_t<int32_t>(d_insts, ninst, d_counter, C, nclusters, smem, flags, st);
+    return launch_solver_t<int16_t>(d_insts, ninst, d_counter, C, nclusters, smem, flags, st,
+                                    quantum_ns, set_attrs);
+  return launch_solver_t<int32_t>(d_insts, ninst, d_counter, C, nclusters, smem, flags, st,
+                                  quantum_ns, set_attrs);
 }
 
 // Largest number of co-resident clusters of size C for this kernel.
@@ -1128,12 +1196,7 @@ static int max_clusters_t(int C, size_t smem) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   auto kern = asral_cluster_kernel<T>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
-    return -1;
-  if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                   cudaSuccess)
-    return -1;
+  if (prepare_solver_t<T>(C, smem) != cudaSuccess) return -1;
   int num = 0;
   return cudaOccupancyMaxActiveClusters(&num, kern, &cfg) == cudaSuccess ? num : -1;
 }

@@ -9,69 +9,34 @@
 #include <mutex>
 #include <vector>
 
-#include "../../include/lbdd.h"
-#include "lbdd_device.cuh"
-
-namespace lbdd {
-size_t solver_smem_bytes(int32_t k, int C, int elem_bytes, bool with_slice);
-int solver_max_k(int C, int elem_bytes);
-int solver_max_clusters(int C, int elem_bytes, size_t smem);
-cudaError_t launch_solver(const DevInst* d_insts, int ninst, int* d_counter, int C,
-                          int nclusters, int elem_bytes, size_t smem, int flags,
-                          cudaStream_t st);
-size_t bt_workspace_bytes(int32_t n, int32_t k);
-int bt_max_k(int elem_bytes);
-cudaError_t best_transfer_run(int32_t n, int32_t k, const void* cm, int elem_bytes, int64_t ld,
-                              const int32_t* assign, int32_t* tc, int32_t* td, void* ws,
-                              cudaStream_t st, int num_sms);
-}  // namespace lbdd
+#include "lbdd_internal.h"
 
 using namespace lbdd;
-
-struct lbdd_solver {
-  int32_t n = 0, k = 0;
-  int elem = 4;
-  int64_t ld = 0;
-  void* cm = nullptr;
-  int32_t *cap = nullptr, *pen = nullptr, *smin = nullptr, *order = nullptr,
-          *sort_tmp = nullptr, *assign = nullptr, *pos = nullptr, *load = nullptr,
-          *seg_size = nullptr, *page_tab = nullptr, *pool = nullptr, *free_stack = nullptr,
-          *tc = nullptr, *td = nullptr, *counter = nullptr;
-  int64_t* ctl = nullptr;
-  DevInst* d_inst = nullptr;
-  DevInst h_inst;
-  cudaStream_t st = nullptr;
-  int cluster = 0;         // 0 = auto
-  int ncyc_skip = 1;
-  int npath_reuse = 1;
-  int tc_smem = 1;
-  int device = 0;
-  int num_sms = 0;
-  std::vector<void*> allocs;
-};
 
 static char g_cuda_err[256] = "no error";
 static std::mutex g_err_mu;
 
-static int cuda_fail(cudaError_t e, const char* what) {
+int lbdd::cuda_fail(cudaError_t e, const char* what) {
   std::lock_guard<std::mutex> lk(g_err_mu);
   snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", what, cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? LBDD_ERR_OOM : LBDD_ERR_CUDA;
 }
 
-#define CK(call)                                   \
-  do {                                             \
-    cudaError_t e_ = (call);                       \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-  } while (0)
+#define CK(call) LBDD_CK(call)
 
+// Device memory of a solver comes from the stream-ordered pool on the
+// solver's stream: allocating and freeing never waits for kernels running on
+// other streams (a server admits and retires requests while others solve).
 static int dev_alloc(lbdd_solver* s, void** p, size_t bytes) {
-  cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+  bytes = std::max<size_t>(bytes, 16);
+  cudaError_t e = cudaMallocAsync(p, bytes, s->st);
   if (e != cudaSuccess) {
     *p = nullptr;
-    return cuda_fail(e, "cudaMalloc");
+    return cuda_fail(e, "cudaMallocAsync");
   }
   s->allocs.push_back(*p);
+  s->sizes.push_back(bytes);
+  s->bytes += bytes;
   return LBDD_OK;
 }
 
@@ -83,12 +48,27 @@ static int dalloc(lbdd_solver* s, P** p, size_t count) {
   return rc;
 }
 
-static void free_all(lbdd_solver* s) {
-  for (void* p : s->allocs) cudaFree(p);
-  s->allocs.clear();
+static void dev_free(lbdd_solver* s, void* p) {
+  for (size_t i = 0; i < s->allocs.size(); ++i) {
+    if (s->allocs[i] == p) {
+      cudaFreeAsync(p, s->st);
+      s->bytes -= s->sizes[i];
+      s->allocs.erase(s->allocs.begin() + i);
+      s->sizes.erase(s->sizes.begin() + i);
+      return;
+    }
+  }
 }
 
-static int check_device(int* dev, int* sms) {
+static void free_all(lbdd_solver* s) {
+  for (void* p : s->allocs) cudaFreeAsync(p, s->st);
+  cudaStreamSynchronize(s->st);
+  s->allocs.clear();
+  s->sizes.clear();
+  s->bytes = 0;
+}
+
+int lbdd::check_device(int* dev, int* sms) {
   CK(cudaGetDevice(dev));
   cudaDeviceProp prop;
   CK(cudaGetDeviceProperties(&prop, *dev));
@@ -137,7 +117,7 @@ extern "C" int64_t lbdd_cm_pitch(int32_t k, int cm_dtype) {
 }
 
 // Copy CM into padded device storage; returns storage, pitch and element size.
-static int ingest_cm(lbdd_solver* s, const void* cm, int dtype, int is_device) {
+static int ingest_cm(lbdd_solver* s, const void* cm, int dtype, int is_device, int64_t src_ld) {
   const int32_t n = s->n, k = s->k;
   const int in_elem = dtype == LBDD_CM_I16 ? 2 : 4;
   const int64_t ld = lbdd_cm_pitch(k, dtype);
@@ -146,7 +126,7 @@ static int ingest_cm(lbdd_solver* s, const void* cm, int dtype, int is_device) {
   int rc = dev_alloc(s, &store, bytes);
   if (rc) return rc;
   CK(cudaMemsetAsync(store, 0, bytes, s->st));
-  CK(cudaMemcpy2DAsync(store, ld * in_elem, cm, (size_t)k * in_elem, (size_t)k * in_elem, n,
+  CK(cudaMemcpy2DAsync(store, ld * in_elem, cm, (size_t)src_ld * in_elem, (size_t)k * in_elem, n,
                        is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->st));
   int* mm = nullptr;
   rc = dalloc(s, &mm, 2);
@@ -173,8 +153,7 @@ static int ingest_cm(lbdd_solver* s, const void* cm, int dtype, int is_device) {
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->st));
     // release the wide copy
-    CK(cudaFree(store));
-    s->allocs.erase(std::find(s->allocs.begin(), s->allocs.end(), store));
+    dev_free(s, store);
     s->cm = narrow;
     s->ld = ld16;
     s->elem = 2;
@@ -195,25 +174,44 @@ static int pick_cluster(const lbdd_solver* s) {
   return std::min(16, p);
 }
 
-constexpr size_t kMaxSmem = 227 * 1024;
-
 // Dynamic shared memory for a launch: with the owned cost slice when it fits.
-static size_t launch_smem(int32_t k, int C, int elem) {
+size_t lbdd::launch_smem(int32_t k, int C, int elem) {
   const size_t full = solver_smem_bytes(k, C, elem, true);
   return full <= kMaxSmem ? full : solver_smem_bytes(k, C, elem, false);
 }
 
-static int fits(const lbdd_solver* s, int C) {
-  const size_t smem = launch_smem(s->k, C, s->elem);
-  if (smem > kMaxSmem) return 0;
-  const int32_t w = (s->k + C - 1) / C;
-  if (w > solver_max_k(1, s->elem)) return 0;
-  return solver_max_clusters(C, s->elem, smem) >= 1;
+bool lbdd::fits_k(int32_t k, int elem, int C) {
+  const size_t smem = launch_smem(k, C, elem);
+  if (smem > kMaxSmem) return false;
+  const int32_t w = (k + C - 1) / C;
+  if (w > solver_max_k(1, elem)) return false;
+  return solver_max_clusters(C, elem, smem) >= 1;
 }
 
-extern "C" int lbdd_create(lbdd_solver** out, int32_t n, int32_t k, const void* cm, int cm_dtype,
-                           int cm_is_device, const int32_t* cap, const int32_t* pen,
-                           void* cuda_stream) {
+static int fits(const lbdd_solver* s, int C) { return fits_k(s->k, s->elem, C) ? 1 : 0; }
+
+size_t lbdd::solver_footprint(int32_t n, int32_t k, int in_elem, int elem) {
+  auto a = [](size_t b) { return (std::max<size_t>(b, 16) + 511) / 512 * 512; };
+  const int dt_in = in_elem == 2 ? LBDD_CM_I16 : LBDD_CM_I32;
+  const int dt = elem == 2 ? LBDD_CM_I16 : LBDD_CM_I32;
+  size_t cm = a(((size_t)n * lbdd_cm_pitch(k, dt_in) + kColPad) * in_elem);
+  if (elem != in_elem) cm += a(((size_t)n * lbdd_cm_pitch(k, dt) + kColPad) * elem);
+  const size_t max_pages = ((size_t)n + kPage - 1) / kPage;
+  const size_t npages = max_pages + k;
+  size_t b = cm + a(8);                       // CM copies + min/max scratch
+  b += 2 * a(4ull * k);                       // cap, pen
+  b += 2 * a(4ull * n) + a(12ull * n);        // smin, order, sort_tmp
+  b += 2 * a(4ull * n);                       // assign, pos
+  b += 2 * a(4ull * k);                       // load, seg_size
+  b += a(4ull * k * max_pages) + a(4ull * npages * kPage) + a(4ull * npages);
+  b += 2 * a(4ull * k * k);                   // tc, td
+  b += a(8ull * CTL_COUNT) + a(16) + a(sizeof(DevInst));
+  return b;
+}
+
+static int create_impl(lbdd_solver** out, int32_t n, int32_t k, const void* cm, int cm_dtype,
+                       int cm_is_device, int64_t cm_ld, const int32_t* cap, const int32_t* pen,
+                       void* cuda_stream) {
   if (!out) return LBDD_ERR_ARG;
   *out = nullptr;
   if (n < 1 || k < 1 || !cm || !cap || !pen) return LBDD_ERR_ARG;
@@ -228,7 +226,7 @@ extern "C" int lbdd_create(lbdd_solver** out, int32_t n, int32_t k, const void* 
   s->st = static_cast<cudaStream_t>(cuda_stream);
   int rc = check_device(&s->device, &s->num_sms);
   if (rc) { delete s; return rc; }
-  rc = ingest_cm(s, cm, cm_dtype, cm_is_device);
+  rc = ingest_cm(s, cm, cm_dtype, cm_is_device, cm_ld);
   if (rc) { free_all(s); delete s; return rc; }
   if (launch_smem(k, 16, s->elem) > kMaxSmem) { free_all(s); delete s; return LBDD_ERR_ARG; }
   const int32_t max_pages = (n + kPage - 1) / kPage;
@@ -274,6 +272,21 @@ extern "C" int lbdd_create(lbdd_solver** out, int32_t n, int32_t k, const void* 
   return LBDD_OK;
 }
 
+extern "C" int lbdd_create(lbdd_solver** out, int32_t n, int32_t k, const void* cm, int cm_dtype,
+                           int cm_is_device, const int32_t* cap, const int32_t* pen,
+                           void* cuda_stream) {
+  return create_impl(out, n, k, cm, cm_dtype, cm_is_device, k, cap, pen, cuda_stream);
+}
+
+int lbdd::clone_solver(const lbdd_solver* src, lbdd_solver** out) {
+  std::vector<int32_t> cap(src->k), pen(src->k);
+  CK(cudaMemcpyAsync(cap.data(), src->cap, 4ull * src->k, cudaMemcpyDeviceToHost, src->st));
+  CK(cudaMemcpyAsync(pen.data(), src->pen, 4ull * src->k, cudaMemcpyDeviceToHost, src->st));
+  CK(cudaStreamSynchronize(src->st));
+  return create_impl(out, src->n, src->k, src->cm, src->elem == 2 ? LBDD_CM_I16 : LBDD_CM_I32, 1,
+                     src->ld, cap.data(), pen.data(), src->st);
+}
+
 extern "C" int lbdd_set_option(lbdd_solver* s, int option, int64_t value) {
   if (!s) return LBDD_ERR_ARG;
   switch (option) {
@@ -301,7 +314,7 @@ extern "C" int lbdd_set_option(lbdd_solver* s, int option, int64_t value) {
 
 // ---------------------------------------------------------------- solve ---
 
-static int status_to_rc(int64_t st) {
+int lbdd::status_to_rc(int64_t st) {
   if (st == 0) return LBDD_OK;
   if (st == ST_ERR_INVARIANT) return LBDD_ERR_INVARIANT;
   return LBDD_ERR_STATE;
@@ -319,12 +332,12 @@ static int set_target(lbdd_solver* s, int64_t max_rounds, cudaStream_t st) {
   return LBDD_OK;
 }
 
-static int solver_flags(const lbdd_solver* s) {
+int lbdd::solver_flags(const lbdd_solver* s) {
   return (s->ncyc_skip ? 0 : OPT_NO_NCYC_SKIP) | (s->npath_reuse ? 0 : OPT_NO_NPATH_REUSE) |
          (s->tc_smem ? 0 : OPT_NO_TC_SMEM);
 }
 
-static int choose_cluster(lbdd_solver* s) {
+int lbdd::choose_cluster(lbdd_solver* s) {
   int C = pick_cluster(s);
   while (C > 1 && !fits(s, C)) C >>= 1;
   return fits(s, C) ? C : 0;
@@ -345,70 +358,35 @@ extern "C" int lbdd_solve(lbdd_solver* s, int64_t max_rounds) {
   return status_to_rc(st);
 }
 
+int lbdd::solve_timed(lbdd_solver* s, int64_t max_rounds, int C, float* ms) {
+  int rc = set_target(s, max_rounds, s->st);
+  if (rc) return rc;
+  if (C < 1 || !fits(s, C)) return LBDD_ERR_ARG;
+  const size_t smem = launch_smem(s->k, C, s->elem);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaMemsetAsync(s->counter, 0, sizeof(int32_t), s->st));
+  CK(prepare_solver(C, s->elem, smem));
+  CK(cudaEventRecord(e0, s->st));
+  CK(launch_solver(s->d_inst, 1, s->counter, C, 1, s->elem, smem, solver_flags(s), s->st, 0,
+                   false));
+  CK(cudaEventRecord(e1, s->st));
+  int64_t st = 0;
+  CK(cudaMemcpyAsync(&st, s->ctl + CTL_STATUS, sizeof(int64_t), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  CK(cudaEventElapsedTime(ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return status_to_rc(st);
+}
+
 extern "C" int lbdd_reset(lbdd_solver* s) {
   if (!s) return LBDD_ERR_ARG;
   CK(cudaMemsetAsync(s->ctl, 0, sizeof(int64_t) * CTL_COUNT, s->st));
   CK(cudaMemsetAsync(s->assign, 0xff, 4ull * s->n, s->st));
   CK(cudaMemsetAsync(s->load, 0, 4ull * s->k, s->st));
   return LBDD_OK;
-}
-
-extern "C" int lbdd_solve_batch(lbdd_solver* const* solvers, int m, int64_t max_rounds,
-                                int cluster_size, int max_clusters, void* stream) {
-  if (!solvers || m < 1 || cluster_size < 0 || cluster_size > 16 || max_clusters < 0)
-    return LBDD_ERR_ARG;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  for (int i = 0; i < m; ++i) {
-    if (!solvers[i]) return LBDD_ERR_ARG;
-    int rc = set_target(solvers[i], max_rounds, st);
-    if (rc) return rc;
-  }
-  int flags = 0;
-  for (int i = 0; i < m; ++i) flags |= solver_flags(solvers[i]);
-  // one persistent launch per element size, largest instances first
-  for (int elem : {2, 4}) {
-    std::vector<lbdd_solver*> group;
-    for (int i = 0; i < m; ++i)
-      if (solvers[i]->elem == elem) group.push_back(solvers[i]);
-    if (group.empty()) continue;
-    std::stable_sort(group.begin(), group.end(), [](const lbdd_solver* a, const lbdd_solver* b) {
-      return (int64_t)a->n * a->k > (int64_t)b->n * b->k;
-    });
-    int32_t kmax = 0;
-    for (auto* g : group) kmax = std::max(kmax, g->k);
-    int C = cluster_size;
-    if (C == 0) {
-      // smallest cluster whose owned cost slice fits in shared memory
-      C = 1;
-      while (C < 16 && solver_smem_bytes(kmax, C, elem, true) > kMaxSmem) C <<= 1;
-    }
-    const size_t smem = launch_smem(kmax, C, elem);
-    if (smem > kMaxSmem || (kmax + C - 1) / C > solver_max_k(1, elem)) return LBDD_ERR_ARG;
-    const int fit = solver_max_clusters(C, elem, smem);
-    if (fit < 1) return LBDD_ERR_ARG;
-    int ncl = std::min<int>((int)group.size(), fit);
-    if (max_clusters > 0) ncl = std::min(ncl, max_clusters);
-    std::vector<DevInst> h;
-    for (auto* g : group) h.push_back(g->h_inst);
-    DevInst* d = nullptr;
-    int32_t* counter = nullptr;
-    CK(cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(DevInst) * h.size(), st));
-    CK(cudaMallocAsync(reinterpret_cast<void**>(&counter), sizeof(int32_t), st));
-    CK(cudaMemcpyAsync(d, h.data(), sizeof(DevInst) * h.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
-    CK(launch_solver(d, (int)h.size(), counter, C, ncl, elem, smem, flags, st));
-    CK(cudaFreeAsync(d, st));
-    CK(cudaFreeAsync(counter, st));
-  }
-  CK(cudaStreamSynchronize(st));
-  int first = LBDD_OK;
-  for (int i = 0; i < m; ++i) {
-    int64_t v = 0;
-    CK(cudaMemcpy(&v, solvers[i]->ctl + CTL_STATUS, sizeof(int64_t), cudaMemcpyDeviceToHost));
-    int rc = status_to_rc(v);
-    if (rc && first == LBDD_OK) first = rc;
-  }
-  return first;
 }
 
 // ------------------------------------------------------------ accessors ---

@@ -1,0 +1,130 @@
+"""GPU parity of batched solves (lbdd_batch_*, lbdd_solve_batch, lbdd_autotune).
+
+A batch only schedules independent runs of Alg. 2, so every instance must
+end with exactly the oracle's allotment and objective, whatever its cluster
+size, group, queue position or how its rounds are split between passes.
+"""
+import numpy as np
+import pytest
+
+import lbdd_inputs as L
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def mix(count, seed0=0, n_range=(2.3, 3.2), k_range=(0.4, 2.2)):
+    """Small instances of the batched mix (n ~ 200..1600, k ~ 2..160)."""
+    return [L.make(L.batch_recipe(seed0 + i, n_range=n_range, k_range=k_range), dtype="i16")
+            for i in range(count)]
+
+
+@pytest.fixture(scope="module")
+def small_mix():
+    insts = mix(16)
+    refs = [oracle.asral(x.cm, x.cap, x.pen) for x in insts]
+    return insts, refs
+
+
+def check(solvers, refs):
+    for s, ref in zip(solvers, refs):
+        assert s.rounds == len(ref.assign)
+        assert s.objective == ref.delta
+        assert np.array_equal(s.assignment(), ref.assign)
+        assert np.array_equal(s.loads().astype(np.int64), ref.load)
+
+
+def test_graph_batch_matches_oracle(gpu_lib, small_mix):
+    insts, refs = small_mix
+    solvers = [gpu_lib.Solver(x.cm, x.cap, x.pen) for x in insts]
+    try:
+        b = gpu_lib.Batch(solvers)
+        cl, groups = b.plan()
+        assert len(cl) == len(insts) and all(c in (1, 2, 4, 8, 16) for c in cl)
+        assert sum(g[2] for g in groups) == len(insts)
+        b.run()
+        check(solvers, refs)
+        b.run()                      # nothing left: a no-op
+        check(solvers, refs)
+        b.close()
+    finally:
+        for s in solvers:
+            s.close()
+
+
+def test_graph_batch_in_slices(gpu_lib, small_mix):
+    """Replaying the graph with a round limit resumes every instance where
+    it stopped."""
+    insts, refs = small_mix
+    solvers = [gpu_lib.Solver(x.cm, x.cap, x.pen) for x in insts]
+    try:
+        b = gpu_lib.Batch(solvers)
+        for _ in range(200):
+            b.run(97)
+            if all(s.rounds == s.n for s in solvers):
+                break
+        check(solvers, refs)
+        b.close()
+    finally:
+        for s in solvers:
+            s.close()
+
+
+@pytest.mark.parametrize("cluster", [1, 2])
+def test_forced_cluster_and_cap(gpu_lib, small_mix, cluster):
+    insts, refs = small_mix
+    solvers = [gpu_lib.Solver(x.cm, x.cap, x.pen) for x in insts]
+    try:
+        gpu_lib.solve_batch([s.h for s in solvers], cluster_size=cluster, max_clusters=3)
+        check(solvers, refs)
+    finally:
+        for s in solvers:
+            s.close()
+
+
+def test_resume_on_another_cluster_size(gpu_lib):
+    """Solver state lives in device memory: a solve may continue on a
+    different cluster size."""
+    inst = L.make_named("tiny")
+    ref = oracle.asral(inst.cm, inst.cap, inst.pen)
+    with gpu_lib.Solver(inst.cm, inst.cap, inst.pen, cluster=1) as s:
+        s.solve(700)
+        gpu_lib.set_option(s.h, gpu_lib.OPT_CLUSTER, 4)
+        s.solve(600)
+        gpu_lib.set_option(s.h, gpu_lib.OPT_CLUSTER, 2)
+        s.solve()
+        assert s.objective == ref.delta
+        assert np.array_equal(s.assignment(), ref.assign)
+
+
+def test_autotune_then_plan(gpu_lib):
+    insts = mix(10, seed0=40, n_range=(2.5, 3.0), k_range=(0.5, 2.3))
+    refs = [oracle.asral(x.cm, x.cap, x.pen) for x in insts]
+    solvers = [gpu_lib.Solver(x.cm, x.cap, x.pen) for x in insts]
+    try:
+        gpu_lib.tune_clear()
+        gpu_lib.autotune(solvers, probe_rounds=64)
+        for s in solvers:
+            assert s.rounds == 0          # autotuning works on clones
+            assert gpu_lib.tune_get(gpu_lib.CM_I16, s.k, 1) > 0
+        b = gpu_lib.Batch(solvers)
+        cl, groups = b.plan()
+        import torch
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        assert sum(c * n for c, n, _ in groups) <= sms
+        b.run()
+        check(solvers, refs)
+        b.close()
+    finally:
+        gpu_lib.tune_clear()
+        for s in solvers:
+            s.close()
+
+
+def test_batch_rejects_bad_arguments(gpu_lib):
+    inst = L.random_small(5, n=30, k=4)
+    with gpu_lib.Solver(inst.cm, inst.cap, inst.pen) as s:
+        with pytest.raises(gpu_lib.LbddError):
+            gpu_lib.Batch([s], cluster_size=3)
+        with pytest.raises(gpu_lib.LbddError):
+            gpu_lib.solve_batch([s], cluster_size=32)
