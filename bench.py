@@ -41,7 +41,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["city", "tiny"], default="city")
+    ap.add_argument("--workload", choices=["city", "tiny", "batch", "serve"], default="city")
+    ap.add_argument("--batch-size", type=int, default=256, help="batch: instances in the mix")
+    ap.add_argument("--seq-every", type=int, default=8,
+                    help="batch: time one-at-a-time solves of every m-th instance (1 = all)")
+    ap.add_argument("--requests", type=int, default=64, help="serve: requests in the stream")
+    ap.add_argument("--large", default="100000x1000",
+                    help="serve: size n x k of the large requests (5%% of the stream)")
+    ap.add_argument("--quantum-us", type=int, default=20000, help="serve: pass length")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: device memory budget")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-rounds", type=int, default=2000,
                     help="rounds of the CPU oracle timed for cpu_baseline")
@@ -351,10 +359,223 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_batch(args):
+    """Batched mix: `batch_size` independent instances (n log-uniform in
+    [1e3, 1e5), k log-uniform in [10, 400), uniform points, capacities summing
+    to 0.9 n, penalties in [50, 500]) solved by one replay of the captured
+    batch graph; compared with the same instances solved one at a time."""
+    import torch
+    import lbdd_inputs as L
+    import paper_2304_06543_gb300 as lb
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    lb.load()
+    m = args.batch_size
+    insts = [L.make(L.batch_recipe(i), dtype="i16") for i in range(m)]
+    solvers = [lb.Solver(x.cm, x.cap, x.pen) for x in insts]
+    t0 = time.perf_counter()
+    lb.autotune(solvers, probe_rounds=256)
+    tune_s = time.perf_counter() - t0
+    batch = lb.Batch(solvers)
+    plan = batch.plan()[1]
+
+    def step():
+        for s in solvers:
+            lb.reset(s.h)
+        batch.run()
+
+    for _ in range(args.warmup):
+        step()
+    objectives = [s.objective for s in solvers]
+    assert all(s.rounds == s.n for s in solvers)
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = _events()
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    assert [s.objective for s in solvers] == objectives, "batched solves are not deterministic"
+    value = m * args.steps / (ms / 1000.0)
+    # one at a time: each instance alone, default (latency-oriented) cluster size
+    seq_ms, seq_idx = 0.0, list(range(0, m, max(1, args.seq_every)))
+    for i in seq_idx:
+        s = solvers[i]
+        s.reset()
+        a, b = _events()
+        a.record()
+        s.solve()
+        b.record()
+        torch.cuda.synchronize()
+        seq_ms += a.elapsed_time(b)
+        assert s.objective == objectives[i], "batched and lone solves differ"
+    seq_value = len(seq_idx) / (seq_ms / 1000.0)
+    # end to end: host CMs -> create -> batch -> allotments back
+    cms = [torch.from_numpy(x.cm).pin_memory() for x in insts]
+    h2d = sum(x.cm.nbytes + x.cap.nbytes + x.pen.nbytes for x in insts)
+    d2h = sum(4 * x.n + 8 for x in insts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hs = [lb.create(x.n, x.k, c.numpy(), x.cap, x.pen) for x, c in zip(insts, cms)]
+    lb.solve_batch(hs)
+    outs = [(lb.assignment(h, x.n), lb.objective(h)) for h, x in zip(hs, insts)]
+    for h in hs:
+        lb.destroy(h)
+    e2e_s = time.perf_counter() - t0
+    assert [o[1] for o in outs] == objectives
+    rounds = sum(x.n for x in insts)
+    line = {
+        "metric": "solves/s (batched mix)", "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int16",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": f"batched mix of {m} instances, n log-uniform [1e3, 1e5), "
+                               "k log-uniform [10, 400), one CUDA-graph replay per step",
+                   "instances": m, "total_rounds": rounds,
+                   "plan_groups_C_clusters_instances": plan, "autotune_s": round(tune_s, 2),
+                   "l2": "CMs total > L2 (1 GB)"},
+        "rounds_per_s": rounds * args.steps / (ms / 1000.0),
+        "sequential": {"value": seq_value, "unit": "solves/s", "instances_timed": len(seq_idx),
+                       "sample": f"every {args.seq_every}-th instance of the mix, alone, "
+                                 "default cluster size", "ms": seq_ms},
+        "batched_over_sequential": value / seq_value,
+        "e2e": {"value": m / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": None, "clocks": clk,
+    }
+    # kernels per replay: set-targets, one persistent launch per group, gather
+    line["gpu_launches"] = args.steps * (2 + len(plan))
+    print(json.dumps(line), flush=True)
+    batch.close()
+    for s in solvers:
+        s.close()
+
+
+def run_serve(args):
+    """Serving stream: Poisson arrivals of `requests` LBDD requests, 95% sized
+    like the batched mix and 5% large (`--large`), through the request server
+    (continuous batching under a device-memory budget), against the same
+    requests solved one at a time in arrival order."""
+    import torch
+    import lbdd_inputs as L
+    import paper_2304_06543_gb300 as lb
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    lb.load()
+    n_l, k_l = (int(v) for v in args.large.lower().split("x"))
+    R = args.requests
+    recs = [L.serve_recipe(i, large=(n_l, k_l)) for i in range(R)]
+    insts = [L.make(r, dtype="i16") for r, _ in recs]
+    large = [bool(b) for _, b in recs]
+    budget = int(args.budget_gb * (1 << 30))
+    # tune the plan on the stream's own sizes (clones; outside every timed region)
+    tune = [lb.Solver(x.cm, x.cap, x.pen) for x in insts]
+    lb.autotune(tune, probe_rounds=256)
+    for s in tune:
+        s.close()
+
+    def serve(arrivals):
+        with lb.Server(budget, quantum_us=args.quantum_us) as srv:
+            t0 = time.perf_counter()
+            tickets = []
+            for i, x in enumerate(insts):
+                dt = arrivals[i] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                tickets.append(srv.submit(x.cm, x.cap, x.pen))
+            res = [srv.result(t) for t in tickets]
+            wall = time.perf_counter() - t0
+            st = srv.stats()
+        lat = [(info.done_ns - info.submit_ns) / 1e6 for info, _ in res]
+        return res, lat, wall, st
+
+    # warm-up: a few small requests
+    small = [i for i in range(R) if not large[i]][:4]
+    with lb.Server(budget, quantum_us=args.quantum_us) as srv:
+        for i in small:
+            srv.result(srv.submit(insts[i].cm, insts[i].cap, insts[i].pen))
+    # 1. saturation: everything arrives at t = 0
+    clocks = ClockSampler(local)
+    clocks.start()
+    res_c, lat_c, wall_c, st_c = serve(np.zeros(R))
+    clk = clocks.stop()
+    objectives = [info.objective for info, _ in res_c]
+    assert all(info.state == lb.REQ_DONE for info, _ in res_c)
+    sat = R / wall_c
+    # 2. Poisson arrivals at 90% of the saturated rate
+    rate = 0.9 * sat
+    arr = L.arrival_times(R, rate)
+    res_p, lat_p, wall_p, st_p = serve(arr)
+    assert [info.objective for info, _ in res_p] == objectives, "served results differ"
+    # 3. one at a time, arrival order: service time of each request alone
+    service = []
+    for i, x in enumerate(insts):
+        t0 = time.perf_counter()
+        h = lb.create(x.n, x.k, x.cm, x.cap, x.pen)
+        lb.solve(h)
+        a = lb.assignment(h, x.n)
+        obj = lb.objective(h)
+        lb.destroy(h)
+        service.append(time.perf_counter() - t0)
+        assert obj == objectives[i], "served and lone solves differ"
+        assert np.array_equal(a, res_c[i][1])
+    seq = R / sum(service)
+    # FIFO single server fed by the same arrivals
+    done, seq_lat = 0.0, []
+    for a_t, s_t in zip(arr, service):
+        start = max(a_t, done)
+        done = start + s_t
+        seq_lat.append((done - a_t) * 1000)
+
+    def pct(v, q):
+        return float(np.percentile(np.asarray(v), q))
+    h2d = sum(x.cm.nbytes + x.cap.nbytes + x.pen.nbytes for x in insts)
+    line = {
+        "metric": "solves/s served vs sequential", "value": sat, "unit": "solves/s",
+        "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": wall_c * 1000,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int16",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": f"serving stream of {R} requests: 95% sized like the batched "
+                               f"mix, 5% large at {n_l}x{k_l}",
+                   "requests": R, "large_requests": int(sum(large)),
+                   "budget_gb": args.budget_gb, "quantum_us": args.quantum_us,
+                   "total_rounds": int(sum(x.n for x in insts))},
+        "served_saturated": {"solves_per_s": sat, "wall_s": wall_c,
+                             "p50_ms": pct(lat_c, 50), "p99_ms": pct(lat_c, 99),
+                             "passes": st_c.passes, "busy_frac": st_c.busy_ns / st_c.uptime_ns,
+                             "peak_active": st_c.peak_active,
+                             "peak_budget_gb": st_c.peak_bytes / 2**30},
+        "served_poisson": {"arrival_rate_per_s": rate, "rate_rule": "0.9 x saturated rate",
+                           "solves_per_s": R / wall_p, "p50_ms": pct(lat_p, 50),
+                           "p99_ms": pct(lat_p, 99), "busy_frac": st_p.busy_ns / st_p.uptime_ns},
+        "sequential": {"solves_per_s": seq, "p50_ms": pct(seq_lat, 50),
+                       "p99_ms": pct(seq_lat, 99),
+                       "latency_rule": "FIFO, same arrivals, measured lone service times"},
+        "served_over_sequential": sat / seq,
+        "e2e": {"value": sat, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": sum(4 * x.n + 8 for x in insts)},
+        "gpu_launches": st_c.launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

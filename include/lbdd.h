@@ -217,6 +217,7 @@ typedef struct lbdd_server_stats {
   int64_t bytes_in_use, peak_bytes;      /* budget held now / at most */
   int64_t busy_ns, uptime_ns;            /* time with a pass in flight / since create */
   int64_t peak_active;                   /* most requests in one pass */
+  int64_t launches;                      /* kernels launched by all passes */
 } lbdd_server_stats;
 /* The server runs on the current device with its own streams and threads. */
 int lbdd_server_create(lbdd_server** out, const lbdd_server_config* cfg);

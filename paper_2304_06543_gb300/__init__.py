@@ -69,7 +69,7 @@ class _RequestInfo(ctypes.Structure):
 
 
 _SERVER_STAT_FIELDS = ("passes", "admitted", "completed", "failed", "queued", "bytes_in_use",
-                       "peak_bytes", "busy_ns", "uptime_ns", "peak_active")
+                       "peak_bytes", "busy_ns", "uptime_ns", "peak_active", "launches")
 
 
 class _ServerStats(ctypes.Structure):
@@ -452,6 +452,7 @@ class ServerStats:
     busy_ns: int
     uptime_ns: int
     peak_active: int
+    launches: int
 
 
 class Server:

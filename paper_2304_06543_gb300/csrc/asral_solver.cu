@@ -33,8 +33,8 @@
 namespace lbdd {
 
 struct Layout {
-  uint32_t dist, hop, load, cap, pen, front, par, outk, ink, incnt, insink, npart, path, pathu,
-      misc, red, tsm, base_total, total;
+  uint32_t dist, hop, load, cap, pen, front, par, outbox, npart, path, pathu, misc, red, tsm,
+      base_total, total;
 };
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -52,6 +52,7 @@ __host__ __device__ inline int32_t slice_stride(int32_t w, int32_t elem) {
 }
 
 constexpr uint32_t kRedBytes = kThreads * 8 * 8;  // rescan partials, int16 CM
+constexpr uint32_t kOutboxExtra = 4;              // outbox slots after the w key slots
 
 // Shared-memory carve-up; `base_total` excludes the cost slice, `total`
 // includes it (k x w entries of elem bytes).
@@ -68,10 +69,7 @@ __host__ __device__ inline Layout make_layout(int32_t k, int32_t C, int32_t elem
   L.pen = o;    o = align16(o + 4u * ku);
   L.front = o;  o = align16(o + 8u * (ku + 1));       // frontier keys of the current sweep
   L.par = o;    o = align16(o + 4u * w);
-  L.outk = o;   o = align16(o + 8u * w);              // this sweep's own changes (keys)
-  L.ink = o;    o = align16(o + 2u * Cu * w * 8u);     // inbox [2][C][w] keys = next frontier
-  L.incnt = o;  o = align16(o + 2u * Cu * 2u * 4u);    // inbox [2][C] {count, merge flag}
-  L.insink = o; o = align16(o + 2u * 4u * 8u);         // inbox [2] sink record
+  L.outbox = o; o = align16(o + 2u * (w + kOutboxExtra) * 8u);   // [2][w + extra] published keys
   L.npart = o;  o = align16(o + Cu * 16u);             // per-CTA partial minima
   L.path = o;   o = align16(o + 4u * (ku + 2));
   L.pathu = o;  o = align16(o + 4u * (ku + 2));
@@ -83,12 +81,13 @@ __host__ __device__ inline Layout make_layout(int32_t k, int32_t C, int32_t elem
   return L;
 }
 
-// Sink record of an inbox buffer.
-enum { SK_CHANGED = 0, SK_DIST, SK_PAR };
+// Outbox of one sweep: w key slots, then these (index w + OB_*).
+enum { OB_MERGE = 0, OB_SINK, OB_SLOTS };
+constexpr uint64_t kNoKey = ~0ull;   // empty slot (no real key has all bits set)
+static_assert(OB_SLOTS <= (int)kOutboxExtra, "outbox extra slots");
 // Slots of the per-CTA scalar block.
-enum { MS_SINK_DIST = 0, MS_SINK_PAR, MS_LCNT0, MS_LCNT1, MS_PATHLEN, MS_OWN_SINK_CHG0,
-       MS_OWN_SINK_CHG1, MS_OWN_SINK_DIST, MS_OWN_SINK_PAR, MS_NAFF, MS_MERGE_ANY, MS_STOP0,
-       MS_STOP1 };
+enum { MS_SINK_DIST = 0, MS_SINK_PAR, MS_LCNT0, MS_LCNT1, MS_PATHLEN, MS_SINK_KEY, MS_NAFF,
+       MS_MERGE_ANY, MS_STOP0, MS_STOP1 };
 
 // Rounds between two checks of the launch's time quantum.
 constexpr int kQuantumCheck = 8;
@@ -125,10 +124,7 @@ struct Solver {
   int32_t* s_pen;     // penalty replica
   uint64_t* s_front;  // frontier keys ((label + 2^47) << 16 | node) of the current sweep
   int32_t* s_par;     // parents of the owned columns
-  uint64_t* s_outk;   // [w] keys of the owned columns improved in this sweep
-  uint64_t* s_ink;    // inbox [2][C][w]: keys ((label + 2^47) << 16 | node) pushed by CTA r
-  int32_t* s_incnt;   // inbox [2][C][2]: {count, merge flag} from CTA r
-  int64_t* s_insink;  // inbox [2][4]: sink record from the owner of column j
+  uint64_t* s_outbox; // [2][w + OB_SLOTS]: keys ((label + 2^47) << 16 | node) published per sweep
   int64_t* s_npart;   // [C][2]: per-CTA partial minima (label; hop << 16 | node)
   int32_t* s_path;
   int32_t* s_pathu;
@@ -476,29 +472,25 @@ struct Solver {
     return best;
   }
 
-  // Strict improvement of owned column cl: record it in the local out list
-  // (pushed to every CTA after the relaxation) or as the sink's new label.
-  // Only the owner reads and writes the label of an owned column.
-  __device__ __forceinline__ void record(int cl, uint64_t best, int32_t j, int64_t sink_dist,
-                                         int sweep, int pb) {
-    if (best == ~0ull) return;
-    const int64_t bc = key_label(best);
-    const int32_t bu = (int32_t)(best & 0xffffu);
+  // Strict improvement of owned column cl.  Returns the frontier key to
+  // publish for it (kNoKey if its label did not improve); the sink column
+  // (v == j) publishes its candidate in the outbox's sink slots instead and
+  // is never a frontier node.  Only the owner reads and writes the label of
+  // an owned column.
+  __device__ __forceinline__ uint64_t record(int cl, uint64_t best, int32_t j, int64_t sink_dist,
+                                             int sweep, uint64_t* ob) {
     const int v = c0 + cl;
-    const int64_t cur = (v == j) ? sink_dist : s_dist[v];
-    if (bc < cur) {
-      if (v == j) {
-        s_misc[MS_OWN_SINK_CHG0 + pb] = 1;
-        s_misc[MS_OWN_SINK_DIST] = bc;
-        s_misc[MS_OWN_SINK_PAR] = bu;
-      } else {
-        const int at = atomicAdd(reinterpret_cast<int*>(&s_misc[MS_LCNT0 + pb]), 1);
-        s_outk[at] = pack_key(bc, v);
-        s_dist[v] = bc;
-        s_hop[v] = sweep;
-        s_par[cl] = bu;
-      }
+    if (v == j) {   // the sink's (label, parent) in the key encoding
+      ob[w + OB_SINK] = best != ~0ull && key_label(best) < sink_dist ? best : kNoKey;
+      return kNoKey;
     }
+    if (best == ~0ull) return kNoKey;
+    const int64_t bc = key_label(best);
+    if (bc >= s_dist[v]) return kNoKey;
+    s_dist[v] = bc;
+    s_hop[v] = sweep;
+    s_par[cl] = (int32_t)(best & 0xffffu);
+    return pack_key(bc, v);
   }
 
   // Canonical synchronous Bellman-Ford from the anchor j (Alg. 3 / Sections
@@ -509,11 +501,14 @@ struct Solver {
   // No edge enters the source.  Labels change only on strict improvement and
   // take the lowest-index predecessor among equal candidates.
   //
-  // Exchange: the owner of a column that improves stores (node, label) into
-  // an inbox of every CTA of the cluster before the sweep's barrier; after
-  // the barrier each CTA applies its local inbox, so the only cross-CTA
-  // operations are remote stores.  Inboxes are double-buffered by sweep
-  // parity: buffer b is rewritten two barriers after it was read.
+  // Exchange: every sweep each CTA writes one outbox slot per owned column
+  // (the improved label's key, or kNoKey) plus its merge flag and, at the
+  // owner of column j, the sink candidate.  After the sweep's cluster barrier
+  // every thread pulls one slot of one CTA through distributed shared memory
+  // and the valid keys are compacted (warp ballots) into the next frontier.
+  // A CTA changes at most w labels per sweep, so the outbox has a fixed size
+  // and needs no counts.  Outboxes are double-buffered by sweep parity: a
+  // buffer is rewritten two barriers after it was read.
   // Returns 1 for a negative sink label (path to apply), 0 for none, and
   // < 0 on a broken invariant.  `merged` says whether this CTA's merge of
   // the round's unit lowered a cost of row j (NegCycle only).
@@ -527,20 +522,21 @@ struct Solver {
       s_dist[j] = 0;
       s_hop[j] = 0;
       s_front[0] = pack_key(0, j);
-      s_misc[MS_LCNT0 + buf] = 0;
-      s_misc[MS_OWN_SINK_CHG0 + buf] = 0;
+      s_misc[MS_LCNT0] = 0;
+      s_misc[MS_LCNT1] = 0;
     }
     __syncthreads();
     const int owner_j = j / w;
     const int32_t pen_j = __ldg(I.pen + j);
+    const int obs = w + (int)kOutboxExtra;
     // lanes own 32 consecutive columns (a column block); the WPB warps of a
     // block split the frontier and their minima are combined in shared memory
     const int CB = max(1, (wr + 31) / 32);
     const int WPB = max(1, kWarps / CB);
     const int lane = tid & 31, warp = tid >> 5;
     uint64_t* red_k = reinterpret_cast<uint64_t*>(s_red + 256);           // [WPB][CB*32]
-    // every thread keeps the same copy of the sink label, the frontier size
-    // and the previous inbox buffer; they change only at cluster barriers
+    // every thread keeps the same copy of the sink label and the frontier
+    // size; they change only at cluster barriers
     int64_t sink_dist = kDInf;
     int32_t sink_par = -1;
     int nfront = 1;
@@ -548,13 +544,15 @@ struct Solver {
     bool skipped_bf = false;
     for (int sweep = 1;; ++sweep) {
       const uint64_t t0 = timer() ? clock_cycles() : 0;
-      const int pb = buf;                      // buffer written in this sweep
+      const int pb = buf;                      // outbox written in this sweep
+      uint64_t* ob = s_outbox + pb * obs;
       if (timer()) {
         B->front_sum += nfront;
         B->front_hist[nfront <= 1 ? 0 : nfront <= 4 ? 1 : nfront <= 16 ? 2 : nfront <= 64 ? 3
                       : nfront <= 256 ? 4 : 5]++;
       }
-      // relax all edges out of the frontier into the owned columns
+      // relax all edges out of the frontier into the owned columns, then
+      // publish every owned column's slot
       if (WPB > 1) {
         const int blk = warp / WPB, slice = warp % WPB;
         if (blk < CB) {
@@ -564,71 +562,69 @@ struct Solver {
         }
         __syncthreads();
         if (timer()) B->t_rloop += clock_cycles() - t0;
-        for (int cl = tid; cl < wr; cl += kThreads) {
-          uint64_t best = ~0ull;
-          for (int sl = 0; sl < WPB; ++sl) best = min(best, red_k[sl * CB * 32 + cl]);
-          record(cl, best, j, sink_dist, sweep, pb);
+        for (int cl = tid; cl < w; cl += kThreads) {
+          uint64_t key = kNoKey;
+          if (cl < wr) {
+            uint64_t best = ~0ull;
+            for (int sl = 0; sl < WPB; ++sl) best = min(best, red_k[sl * CB * 32 + cl]);
+            key = record(cl, best, j, sink_dist, sweep, ob);
+          }
+          ob[cl] = key;
         }
       } else {
         for (int blk = warp; blk < CB; blk += kWarps) {
           const int cl = blk * 32 + lane;
           const uint64_t best = relax_column(cl, cl < wr, 0, 1, nfront, j, npath, pen_j);
-          if (cl < wr) record(cl, best, j, sink_dist, sweep, pb);
+          if (cl < w) ob[cl] = cl < wr ? record(cl, best, j, sink_dist, sweep, ob) : kNoKey;
         }
+        for (int cl = CB * 32 + tid; cl < w; cl += kThreads) ob[cl] = kNoKey;
+        if (timer()) B->t_rloop += clock_cycles() - t0;
       }
-      __syncthreads();
+      if (tid == 0) {
+        ob[w + OB_MERGE] = merged ? 1 : 0;
+        if (rank != owner_j) ob[w + OB_SINK] = kNoKey;
+      }
       if (timer()) B->t_rred += clock_cycles() - t0;
-      // push this CTA's changes into every CTA's inbox buffer pb (all threads
-      // help), then prepare the other buffer's local counters for the next
-      // sweep; both happen before the barrier, so no sweep can see them early
-      {
-        uint64_t* ink = s_ink + pb * C * w;
-        int32_t* incnt = s_incnt + pb * C * 2;
-        int64_t* insink = s_insink + pb * 4;
-        const int cnt = (int)s_misc[MS_LCNT0 + pb];
-        for (int i = tid; i < cnt * C; i += kThreads) {
-          const int e = i / C, r = i - e * C;
-          dsmem_st64(dsmem_addr(ink + rank * w + e, r), (int64_t)s_outk[e]);
-        }
-        if (tid >= kThreads - 32 && tid - (kThreads - 32) < C) {
-          const uint32_t r = tid - (kThreads - 32);
-          dsmem_st32(dsmem_addr(incnt + rank * 2, r), cnt);
-          dsmem_st32(dsmem_addr(incnt + rank * 2 + 1, r), merged ? 1 : 0);
-        }
-        if (rank == owner_j && tid >= kThreads - 64 && tid - (kThreads - 64) < C) {
-          const uint32_t r = tid - (kThreads - 64);
-          dsmem_st64(dsmem_addr(insink + SK_CHANGED, r), s_misc[MS_OWN_SINK_CHG0 + pb]);
-          dsmem_st64(dsmem_addr(insink + SK_DIST, r), s_misc[MS_OWN_SINK_DIST]);
-          dsmem_st64(dsmem_addr(insink + SK_PAR, r), s_misc[MS_OWN_SINK_PAR]);
-        }
-        if (tid == 0) {
-          s_misc[MS_LCNT0 + (pb ^ 1)] = 0;
-          s_misc[MS_OWN_SINK_CHG0 + (pb ^ 1)] = 0;
-        }
-      }
       const uint64_t t1 = timer() ? clock_cycles() : 0;
       cluster_sync_all();
       const uint64_t t2 = timer() ? clock_cycles() : 0;
       commit_pending();
-      // read the local inbox (every thread, same values in every CTA)
-      const int32_t* incnt = s_incnt + pb * C * 2;
-      const int64_t* insink = s_insink + pb * 4;
-      int total = 0;
-      bool any_merge = false;
-      for (int r = 0; r < C; ++r) { total += incnt[2 * r]; any_merge |= incnt[2 * r + 1] != 0; }
-      const bool sink_chg = insink[SK_CHANGED] != 0;
-      if (sink_chg) { sink_dist = insink[SK_DIST]; sink_par = (int32_t)insink[SK_PAR]; }
-      nfront = total;
-      // the inbox segments become the next frontier (a local copy)
-      {
-        const uint64_t* ink = s_ink + pb * C * w;
-        int r = 0, base = 0, cr = C > 0 ? incnt[0] : 0;
-        for (int i = tid; i < total; i += kThreads) {
-          while (i >= base + cr) { base += cr; ++r; cr = incnt[2 * r]; }
-          s_front[i] = ink[r * w + (i - base)];
+      // pull every CTA's outbox: one slot per thread, valid keys compacted
+      // into the next frontier (its order is irrelevant: relaxation takes a
+      // minimum); counter pb was zeroed after the previous barrier
+      int* cnt = reinterpret_cast<int*>(&s_misc[MS_LCNT0 + pb]);
+      if (tid == 0) s_misc[MS_LCNT0 + (pb ^ 1)] = 0;
+      const int nslots = C * w;
+      for (int base = warp * 32; base < nslots; base += kThreads) {
+        const int idx = base + lane;
+        uint64_t key = kNoKey;
+        if (idx < nslots) {
+          const int r = idx / w;
+          key = (uint64_t)dsmem_ld64(dsmem_addr(s_outbox + pb * obs + (idx - r * w), (uint32_t)r));
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, key != kNoKey);
+        if (m != 0u) {
+          int at = 0;
+          if (lane == 0) at = atomicAdd(cnt, __popc(m));
+          at = __shfl_sync(0xffffffffu, at, 0);
+          if (key != kNoKey) s_front[at + __popc(m & ((1u << lane) - 1u))] = key;
         }
       }
-      __syncthreads();
+      bool my_merge = false;
+      if (tid < C)
+        my_merge = dsmem_ld64(dsmem_addr(s_outbox + pb * obs + w + OB_MERGE, (uint32_t)tid)) != 0;
+      if (tid == kThreads - 32)
+        s_misc[MS_SINK_KEY] =
+            dsmem_ld64(dsmem_addr(s_outbox + pb * obs + w + OB_SINK, (uint32_t)owner_j));
+      const bool any_merge = __syncthreads_or(my_merge) != 0;
+      const int total = *cnt;
+      const uint64_t sink_key = (uint64_t)s_misc[MS_SINK_KEY];
+      const bool sink_chg = sink_key != kNoKey;
+      if (sink_chg) {
+        sink_dist = key_label(sink_key);
+        sink_par = (int32_t)(sink_key & 0xffffu);
+      }
+      nfront = total;
       if (timer()) {
         const uint64_t t3 = clock_cycles();
         B->t_relax += t1 - t0;
@@ -1075,11 +1071,8 @@ asral_cluster_kernel(const DevInst* __restrict__ insts, int ninst, int* work_cou
     S.s_cap = reinterpret_cast<int32_t*>(base + L.cap);
     S.s_pen = reinterpret_cast<int32_t*>(base + L.pen);
     S.s_par = reinterpret_cast<int32_t*>(base + L.par);
-    S.s_outk = reinterpret_cast<uint64_t*>(base + L.outk);
     S.s_front = reinterpret_cast<uint64_t*>(base + L.front);
-    S.s_ink = reinterpret_cast<uint64_t*>(base + L.ink);
-    S.s_incnt = reinterpret_cast<int32_t*>(base + L.incnt);
-    S.s_insink = reinterpret_cast<int64_t*>(base + L.insink);
+    S.s_outbox = reinterpret_cast<uint64_t*>(base + L.outbox);
     S.s_npart = reinterpret_cast<int64_t*>(base + L.npart);
     S.s_path = reinterpret_cast<int32_t*>(base + L.path);
     S.s_pathu = reinterpret_cast<int32_t*>(base + L.pathu);

@@ -431,6 +431,7 @@ int batch_wait(lbdd_batch* b, int* first_rc) {
   return LBDD_OK;
 }
 
+int batch_launches(const lbdd_batch* b) { return 2 + (int)b->groups.size(); }
 int64_t batch_rounds(const lbdd_batch* b, int i) { return b->h_out[2 * b->slot_of[i] + 1]; }
 int64_t batch_status(const lbdd_batch* b, int i) { return b->h_out[2 * b->slot_of[i]]; }
 void batch_destroy(lbdd_batch* b) {

@@ -42,6 +42,7 @@ int batch_set(lbdd_batch* b, lbdd_solver* const* solvers, const int64_t* rem, in
               int cluster_size, int max_clusters, bool shortest_first);
 int batch_launch(lbdd_batch* b, int64_t max_rounds);
 int batch_wait(lbdd_batch* b, int* first_rc);
+int batch_launches(const lbdd_batch* b);
 int64_t batch_rounds(const lbdd_batch* b, int i);
 int64_t batch_status(const lbdd_batch* b, int i);
 void batch_destroy(lbdd_batch* b);
@@ -94,7 +95,7 @@ struct lbdd_server {
   bool stop = false;
 
   // counters (under mu)
-  int64_t passes = 0, admitted = 0, completed = 0, failed = 0;
+  int64_t passes = 0, admitted = 0, completed = 0, failed = 0, launches = 0;
   size_t peak_bytes = 0;
   int64_t busy_ns = 0;                // time with a pass in flight
   int peak_active = 0;
@@ -233,6 +234,7 @@ static void engine_loop(lbdd_server* S) {
     const int64_t t_b = now_ns(S->t0);
     lk.lock();
     S->passes++;
+    if (!rc) S->launches += batch_launches(S->batch);
     S->busy_ns += t_b - t_a;
     std::vector<Request*> keep;
     for (size_t i = 0; i < active.size(); ++i) {
@@ -363,6 +365,7 @@ extern "C" int lbdd_server_get_stats(lbdd_server* S, lbdd_server_stats* out) {
   out->busy_ns = S->busy_ns;
   out->uptime_ns = now_ns(S->t0);
   out->peak_active = S->peak_active;
+  out->launches = S->launches;
   return LBDD_OK;
 }
 

@@ -7,7 +7,7 @@ and 2 are not reproducible from the text), so these files pin the oracle's
 own canonical results for regression and for GPU parity at sizes where
 re-running the oracle inside a test would take too long.
 
-Usage:  python tests/golden/make_golden.py tiny [city [rounds]]
+Usage:  python tests/golden/make_golden.py tiny | city [rounds] | batch [count [procs]]
 """
 from __future__ import annotations
 
@@ -63,8 +63,47 @@ def run(name: str, rounds: int = -1) -> dict:
     return out
 
 
+def _batch_one(i: int) -> dict:
+    inst = lbdd_inputs.make(lbdd_inputs.batch_recipe(i))
+    t0 = time.time()
+    res = oracle.asral(inst.cm, inst.cap, inst.pen, mode=oracle.MODE_HEAP)
+    if res.rc != oracle.OK:
+        raise RuntimeError(f"oracle failed on instance {i}: {res.rc}")
+    return {"i": i, "n": inst.n, "k": inst.k, "seed": inst.recipe.seed, "delta": res.delta,
+            "assign_sha256": digest(res.assign.astype(np.int32)),
+            "oracle_seconds": round(time.time() - t0, 2)}
+
+
+def run_batch(count: int = 256, procs: int = 4) -> None:
+    """Oracle results of the batched mix (instance i: lbdd_inputs.batch_recipe(i)),
+    one process per instance at a time; written when all are done."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    # largest first, so that the long ones do not end up last
+    order = sorted(range(count), key=lambda i: -lbdd_inputs.batch_recipe(i).n *
+                   lbdd_inputs.batch_recipe(i).k)
+    with ctx.Pool(procs) as pool:
+        rows = []
+        for r in pool.imap_unordered(_batch_one, order):
+            rows.append(r)
+            print(f"{len(rows)}/{count} instance {r['i']} n={r['n']} k={r['k']} "
+                  f"{r['oracle_seconds']}s", flush=True)
+    rows.sort(key=lambda r: r["i"])
+    path = os.path.join(HERE, f"batch{count}_oracle.json")
+    with open(path, "w") as f:
+        json.dump({"workload": f"batched mix, instances 0..{count - 1} of "
+                               "lbdd_inputs.batch_recipe", "oracle_mode": "heap",
+                   "source": "oracle.asral (CPU), written by tests/golden/make_golden.py",
+                   "instances": rows}, f, indent=0)
+        f.write("\n")
+    print(path)
+
+
 if __name__ == "__main__":
     args = sys.argv[1:] or ["tiny"]
     name = args[0]
-    rounds = int(args[1]) if len(args) > 1 else -1
-    run(name, rounds)
+    if name == "batch":
+        run_batch(int(args[1]) if len(args) > 1 else 256, int(args[2]) if len(args) > 2 else 4)
+    else:
+        rounds = int(args[1]) if len(args) > 1 else -1
+        run(name, rounds)

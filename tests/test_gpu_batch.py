@@ -128,3 +128,27 @@ def test_batch_rejects_bad_arguments(gpu_lib):
             gpu_lib.Batch([s], cluster_size=3)
         with pytest.raises(gpu_lib.LbddError):
             gpu_lib.solve_batch([s], cluster_size=32)
+
+
+def test_full_batched_mix_matches_oracle_golden(gpu_lib):
+    """The 256-instance batched mix (n log-uniform in [1e3, 1e5), k in
+    [10, 400)), one graph replay, against the stored oracle results."""
+    import hashlib
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "batch256_oracle.json")))["instances"]
+    insts = [L.make(L.batch_recipe(i), dtype="i16") for i in range(len(gold))]
+    solvers = [gpu_lib.Solver(x.cm, x.cap, x.pen) for x in insts]
+    try:
+        b = gpu_lib.Batch(solvers)
+        b.run()
+        for g, x, s in zip(gold, insts, solvers):
+            assert (g["n"], g["k"]) == (x.n, x.k)
+            assert s.objective == g["delta"], g["i"]
+            a = s.assignment().astype(np.int32)
+            assert hashlib.sha256(a.tobytes()).hexdigest() == g["assign_sha256"], g["i"]
+        b.close()
+    finally:
+        for s in solvers:
+            s.close()
