@@ -102,6 +102,9 @@ typedef enum lbdd_option {
   LBDD_OPT_NPATH_REUSE = 3, /* 1 (default): answer Alg. 4 from the converged labels of
                                an Alg. 1 run that applied nothing; 0: always run a
                                separate Bellman-Ford */
+  LBDD_OPT_PHASE_TIMERS = 5,/* 0 (default): only the total time of the rounds is kept;
+                               1: also time every phase (the *_ns fields of lbdd_stats
+                               and the frontier counters), which slows the rounds */
 } lbdd_option;
 
 /* Create a solver for one LBDD instance (Section 2.1 inputs).

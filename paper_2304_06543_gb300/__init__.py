@@ -29,7 +29,7 @@ OK = 0
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_INVARIANT, ERR_STATE, ERR_NODEV, ERR_BUDGET = \
     -1, -2, -3, -4, -5, -6, -7, -8
 CM_I32, CM_I16 = 0, 1
-OPT_CLUSTER, OPT_NCYC_SKIP, OPT_NPATH_REUSE, OPT_TC_SMEM = 1, 2, 3, 4
+OPT_CLUSTER, OPT_NCYC_SKIP, OPT_NPATH_REUSE, OPT_TC_SMEM, OPT_PHASE_TIMERS = 1, 2, 3, 4, 5
 TINF = 2**31 - 1
 
 _lib = None
@@ -306,7 +306,7 @@ class Solver:
     """RAII wrapper around one lbdd_solver handle."""
 
     def __init__(self, cm, cap, pen, stream=None, cluster: int = 0, ncyc_skip: bool = True,
-                 npath_reuse: bool = True):
+                 npath_reuse: bool = True, phase_timers: bool = False):
         if isinstance(cm, np.ndarray):
             n, k = cm.shape
         else:
@@ -319,6 +319,8 @@ class Solver:
             set_option(self.h, OPT_NCYC_SKIP, 0)
         if not npath_reuse:
             set_option(self.h, OPT_NPATH_REUSE, 0)
+        if phase_timers:
+            set_option(self.h, OPT_PHASE_TIMERS, 1)
 
     def solve(self, max_rounds: int = -1):
         solve(self.h, max_rounds)

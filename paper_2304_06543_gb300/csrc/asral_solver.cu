@@ -136,7 +136,11 @@ struct Solver {
   Book* B;            // CTA 0 thread 0 bookkeeping (shared memory)
   int32_t pending_d = -1, pending_j = -1;
 
-  __device__ __forceinline__ bool timer() const { return rank == 0 && tid == 0; }
+  // Phase timers run on CTA 0's thread 0, on the path every other CTA waits
+  // for at the cluster barriers, so they are off unless asked for.
+  __device__ __forceinline__ bool timer() const {
+    return (flags & OPT_PHASE_TIMERS) && rank == 0 && tid == 0;
+  }
   __device__ __forceinline__ const T* row(int32_t d) const { return cm + (int64_t)d * I.ld; }
 
   __device__ __forceinline__ int32_t* mslot(int32_t c, int32_t idx) const {
@@ -882,8 +886,8 @@ struct Solver {
 
   // ---------------------------------------------------------- the loop --
   __device__ void run_rounds() {
-    const uint64_t tstart = timer() ? gtimer_ns() : 0;
-    const uint64_t cstart = timer() ? clock_cycles() : 0;
+    const uint64_t tstart = rank == 0 && tid == 0 ? gtimer_ns() : 0;
+    const uint64_t cstart = rank == 0 && tid == 0 ? clock_cycles() : 0;
     const int64_t r_begin = I.ctl[CTL_ROUNDS];
     const int64_t r_end = min((int64_t)n, I.ctl[CTL_TARGET]);
     for (int v = tid; v < k; v += kThreads) {
@@ -935,7 +939,7 @@ struct Solver {
         // first Bellman-Ford sweep), when every CTA has finished reading
         // them for the previous round's rescans.
         B->delta += (int64_t)row(d)[j] + (over ? (int64_t)__ldg(I.pen + j) : 0);
-        B->t_merge += clock_cycles() - tm0;
+        if (timer()) B->t_merge += clock_cycles() - tm0;
       }
       __syncthreads();
       // Alg. 1 at j

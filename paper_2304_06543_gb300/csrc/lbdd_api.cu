@@ -307,6 +307,10 @@ extern "C" int lbdd_set_option(lbdd_solver* s, int option, int64_t value) {
       if (value != 0 && value != 1) return LBDD_ERR_ARG;
       s->npath_reuse = (int)value;
       return LBDD_OK;
+    case LBDD_OPT_PHASE_TIMERS:
+      if (value != 0 && value != 1) return LBDD_ERR_ARG;
+      s->phase_timers = (int)value;
+      return LBDD_OK;
     default:
       return LBDD_ERR_ARG;
   }
@@ -334,7 +338,7 @@ static int set_target(lbdd_solver* s, int64_t max_rounds, cudaStream_t st) {
 
 int lbdd::solver_flags(const lbdd_solver* s) {
   return (s->ncyc_skip ? 0 : OPT_NO_NCYC_SKIP) | (s->npath_reuse ? 0 : OPT_NO_NPATH_REUSE) |
-         (s->tc_smem ? 0 : OPT_NO_TC_SMEM);
+         (s->tc_smem ? 0 : OPT_NO_TC_SMEM) | (s->phase_timers ? OPT_PHASE_TIMERS : 0);
 }
 
 int lbdd::choose_cluster(lbdd_solver* s) {

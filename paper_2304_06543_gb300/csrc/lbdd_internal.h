@@ -46,6 +46,7 @@ struct lbdd_solver {
   int ncyc_skip = 1;
   int npath_reuse = 1;
   int tc_smem = 1;
+  int phase_timers = 0;
   int device = 0;
   int num_sms = 0;
   size_t bytes = 0;        // device bytes held now

@@ -52,6 +52,20 @@ def test_tiny_matches_golden(gpu_lib, cluster):
     assert st.moves == gold["stats"]["moves"]
 
 
+def test_phase_timers_change_nothing_but_stats(gpu_lib):
+    inst = L.make_named("tiny")
+    with open(os.path.join(GOLD, "tiny_oracle.json")) as f:
+        gold = json.load(f)
+    for timers in (False, True):
+        with gpu_lib.Solver(inst.cm, inst.cap, inst.pen, phase_timers=timers) as s:
+            s.solve()
+            st = s.stats()
+            assert s.objective == gold["delta"]
+            assert sha(s.assignment().astype(np.int32)) == gold["assign_sha256"]
+            assert st.rounds_ns > 0
+            assert (st.relax_ns > 0) == timers and (st.front_sum > 0) == timers
+
+
 def test_tiny_without_skip_and_int32_storage(gpu_lib):
     inst = L.make_named("tiny")
     ref = oracle.asral(inst.cm, inst.cap, inst.pen)
