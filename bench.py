@@ -41,7 +41,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["city", "tiny", "batch", "serve"], default="city")
+    ap.add_argument("--workload", choices=["city", "tiny", "batch", "serve", "large"],
+                    default="city")
+    ap.add_argument("--large-rounds", type=int, default=20000,
+                    help="large: solver rounds timed on the 2,000,000 x 2,000 instance")
     ap.add_argument("--batch-size", type=int, default=256, help="batch: instances in the mix")
     ap.add_argument("--seq-every", type=int, default=8,
                     help="batch: time one-at-a-time solves of every m-th instance (1 = all)")
@@ -576,6 +579,99 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def _scan_gbs(lb, cm_dev, cm_dtype, ld, n, k, assign, reps=20):
+    """Device time of lbdd_best_transfer over the whole CM (ms per call)."""
+    import torch
+    tc = torch.empty(k * k, dtype=torch.int32, device="cuda")
+    td = torch.empty_like(tc)
+    wsb = lb.best_transfer_workspace(n, k)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        lb.best_transfer(n, k, cm_dev, cm_dtype, ld, assign, tc, td, ws, wsb)
+    e0, e1 = _events()
+    e0.record()
+    for _ in range(reps):
+        lb.best_transfer(n, k, cm_dev, cm_dtype, ld, assign, tc, td, ws, wsb)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, tc, td
+
+
+def run_large(args):
+    """HBM-bound configuration: |D| = 2,000,000 x |S| = 2,000 (clustered
+    demand, road factors, Zipf capacities summing to 0.85 n, penalties in
+    [100, 5000]).  (1) The standalone best-transfer scan over the whole CM
+    for the s_min allotment, int16 (8 GB) and int32 (16 GB); (2) the solver's
+    rounds/s over the first `large_rounds` rounds."""
+    import torch
+    import lbdd_inputs as L
+    import paper_2304_06543_gb300 as lb
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    lb.load()
+    hbm_peak, peak_kind = peaks()
+    inst = L.make_named("large", dtype="i16")
+    n, k = inst.n, inst.k
+    clocks = ClockSampler(local)
+    clocks.start()
+    scans = {}
+    for dt in ("i16", "i32"):
+        cmd = lb.CM_I16 if dt == "i16" else lb.CM_I32
+        ld = lb.cm_pitch(k, cmd)
+        assert ld == k
+        tdt = torch.int16 if dt == "i16" else torch.int32
+        buf = torch.zeros(n * ld + 128, dtype=tdt, device="cuda")
+        src = torch.from_numpy(inst.cm.reshape(-1))
+        chunk = 1 << 28
+        for a in range(0, n * k, chunk):       # host int16 -> device (widened on the device)
+            b = min(a + chunk, n * k)
+            buf[a:b].copy_(src[a:b].cuda().to(tdt))
+        cm2 = buf[: n * k].view(n, k)
+        assign = torch.argmin(cm2, dim=1).to(torch.int32)   # s_min, lowest index on ties
+        ms, tc, td = _scan_gbs(lb, buf, cmd, ld, n, k, assign)
+        w = 2 if dt == "i16" else 4
+        byts = n * k * w + 4 * n
+        gbs = byts / ms / 1e6
+        scans[dt] = {"ms": ms, "bytes": byts, "achieved_gbs": gbs, "frac": gbs / hbm_peak,
+                     "table_sha256": hashlib.sha256(tc.cpu().numpy().tobytes() +
+                                                    td.cpu().numpy().tobytes()).hexdigest()}
+        del buf, cm2, assign, tc, td
+        torch.cuda.empty_cache()
+    assert scans["i16"]["table_sha256"] == scans["i32"]["table_sha256"]
+    # solver prefix
+    solver = lb.Solver(inst.cm, inst.cap, inst.pen)
+    solver.solve(0)                      # prologue (s_min and the MinDistance order)
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record()
+    solver.solve(args.large_rounds)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    st = solver.stats()
+    rounds = solver.rounds
+    solver.close()
+    line = {
+        "metric": "scan GB/s vs HBM (large)", "value": scans["i16"]["achieved_gbs"],
+        "unit": "GB/s", "n_gpus": world, "steps": 20, "warmup": 3,
+        "ms_per_step": scans["i16"]["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int16", "data": "synthetic (seeded generator)",
+        "config": {"workload": "HBM-bound large instance |D|=2,000,000 x |S|=2,000, "
+                               "best-transfer scan of the s_min allotment; solver prefix",
+                   "n": n, "k": k, "l2": "CM 8 GB / 16 GB > L2"},
+        "roofline": {"kernel": "lbdd_best_transfer (all stages)", "bound": "hbm",
+                     "achieved": scans["i16"]["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                     "frac": scans["i16"]["frac"], "peak_kind": peak_kind, "traffic": None},
+        "scan": scans,
+        "solver_prefix": {"rounds": rounds, "ms": ms, "rounds_per_s": rounds / (ms / 1000.0),
+                          "bf_sweeps_per_round": st.bf_sweeps / max(1, rounds),
+                          "cluster_size": st.cluster_size},
+        "gpu_launches": 2 * 20 * 10 + 1, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -584,6 +680,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "large":
+        run_large(args)
     else:
         run_ours(args)
 

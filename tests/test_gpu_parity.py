@@ -190,3 +190,36 @@ def test_rejects_bad_input(gpu_lib):
         gpu_lib.Solver(cm, np.array([1, 0, 1], np.int32), pen)
     with pytest.raises(gpu_lib.LbddError):
         gpu_lib.Solver(cm, cap, np.array([1, 1, -2], np.int32))
+
+
+def test_city_full_solve_matches_golden(gpu_lib):
+    """The whole city-scale solve (200,000 x 500, every round) against the
+    stored oracle result."""
+    inst = L.make_named("city", dtype="i16")
+    with open(os.path.join(GOLD, "city_oracle.json")) as f:
+        gold = json.load(f)
+    assert sha(inst.cm.astype(np.int32)) == gold["cm_sha256"]
+    with gpu_lib.Solver(inst.cm, inst.cap, inst.pen) as s:
+        s.solve()
+        assert s.rounds == inst.n
+        assert s.objective == gold["delta"]
+        assert sha(s.assignment().astype(np.int32)) == gold["assign_sha256"]
+        assert sha(s.loads().astype(np.int64)) == gold["load_sha256"]
+        st = s.stats()
+        assert st.cycles_applied == gold["stats"]["cycles_applied"]
+        assert st.paths_applied == gold["stats"]["paths_applied"]
+        assert st.moves == gold["stats"]["moves"]
+
+
+def test_large_prefix_matches_golden(gpu_lib):
+    """The 2,000,000 x 2,000 instance (CM 8 GB as int16): prologue over the
+    whole CM and the first 200 rounds against the stored oracle result."""
+    inst = L.make_named("large", dtype="i16")
+    with open(os.path.join(GOLD, "large_r200_oracle.json")) as f:
+        gold = json.load(f)
+    assert (inst.n, inst.k, inst.recipe.seed) == (gold["n"], gold["k"], gold["seed"])
+    with gpu_lib.Solver(inst.cm, inst.cap, inst.pen) as s:
+        s.solve(gold["rounds"])
+        assert s.objective == gold["delta"]
+        assert sha(s.assignment().astype(np.int32)) == gold["assign_sha256"]
+        assert sha(s.loads().astype(np.int64)) == gold["load_sha256"]
