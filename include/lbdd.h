@@ -283,7 +283,9 @@ const char* lbdd_last_cuda_error(void);
  * with the tc/td encoding of lbdd_best_transfer_table.
  *   cm_dev     : device CM, rows of ld >= k elements, ld*elem a multiple of
  *                16 bytes, the allocation readable for 128 elements past the
- *                last row; cm_dtype an lbdd_cm_dtype.
+ *                last row; cm_dtype an lbdd_cm_dtype.  Entries are positive
+ *                (Section 2: CM holds positive integers); the int16 scan
+ *                relies on it (every difference then fits 16 bits).
  *   assign_dev : device int32[n], values in [-1, k).
  *   tc_dev, td_dev : device int32[k*k] outputs.
  *   workspace  : device scratch of lbdd_best_transfer_workspace(n, k) bytes,

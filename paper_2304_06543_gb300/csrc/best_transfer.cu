@@ -37,6 +37,7 @@ struct BtWorkspace {
   unsigned long long* t64;      // k x k packed (cost + 2^31) << 32 | d
   int4* items;                  // explicit work items {center, first row, rows, 0}
   int* err;                     // [0] unused, [1] the work-item queue counter
+  int32_t* dsum;                // 256 digit totals of a radix pass
   int64_t ntiles;
   size_t bytes;
 };
@@ -63,6 +64,7 @@ static BtWorkspace carve(void* base, int32_t n, int32_t k) {
   W.t64 = reinterpret_cast<unsigned long long*>(take(8ull * k * k));
   W.items = reinterpret_cast<int4*>(take(16ull * ((size_t)n / kChunk + (size_t)k + 1)));
   W.err = reinterpret_cast<int*>(take(16));   // err, then the item queue counter
+  W.dsum = reinterpret_cast<int32_t*>(take(4 * 256));
   W.bytes = o;
   return W;
 }
@@ -118,6 +120,76 @@ __global__ void __launch_bounds__(kThreads) bt_scan(int32_t* a, int64_t m, int32
   __syncthreads();
   int32_t run = part[threadIdx.x];
   for (int64_t i = lo; i < hi; ++i) { int32_t c = a[i]; a[i] = run; run += c; }
+}
+
+// Block-wide exclusive scan of one value per thread; returns this thread's
+// prefix and writes the block total to *total.
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* s_warp,
+                                                        int32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t x = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int32_t w = lane < kWarps ? s_warp[lane] : 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, w, off);
+      if (lane >= off) w += y;
+    }
+    if (lane < kWarps) s_warp[lane] = w;   // inclusive warp prefixes
+  }
+  __syncthreads();
+  const int32_t before = warp > 0 ? s_warp[warp - 1] : 0;
+  *total = s_warp[kWarps - 1];
+  return before + x - v;
+}
+
+// Digit totals of a radix pass: CTA d sums row d of the digit-major
+// histogram (one row per digit, one column per tile).
+__global__ void __launch_bounds__(kThreads) bt_digit_sums(const int32_t* __restrict__ tile_hist,
+                                                          int64_t ntiles, int32_t* dsum) {
+  __shared__ int32_t s_warp[kWarps];
+  const int32_t* row = tile_hist + (int64_t)blockIdx.x * ntiles;
+  int32_t s = 0;
+  for (int64_t i = threadIdx.x; i < ntiles; i += kThreads) s += row[i];
+  int32_t total;
+  block_exclusive_scan(s, s_warp, &total);
+  if (threadIdx.x == 0) dsum[blockIdx.x] = total;
+}
+
+// Exclusive scan of the whole digit-major histogram, one CTA per digit row:
+// the row's base is the sum of the lower digits' totals, then the row is
+// scanned in contiguous per-thread chunks.
+__global__ void __launch_bounds__(kThreads) bt_digit_scan(int32_t* tile_hist, int64_t ntiles,
+                                                          const int32_t* __restrict__ dsum) {
+  __shared__ int32_t s_warp[kWarps];
+  __shared__ int32_t s_base;
+  const int d = blockIdx.x;
+  int32_t b = threadIdx.x < d ? dsum[threadIdx.x] : 0;   // d <= 255 < kThreads
+  int32_t btot;
+  block_exclusive_scan(b, s_warp, &btot);
+  if (threadIdx.x == 0) s_base = btot;
+  __syncthreads();
+  const int32_t base = s_base;
+  int32_t* row = tile_hist + (int64_t)d * ntiles;
+  const int64_t per = (ntiles + kThreads - 1) / kThreads;
+  const int64_t lo = min(ntiles, (int64_t)threadIdx.x * per), hi = min(ntiles, lo + per);
+  int32_t s = 0;
+  for (int64_t i = lo; i < hi; ++i) s += row[i];
+  int32_t total;
+  __syncthreads();                     // s_warp is reused
+  int32_t run = base + block_exclusive_scan(s, s_warp, &total);
+  for (int64_t i = lo; i < hi; ++i) {
+    const int32_t c = row[i];
+    row[i] = run;
+    run += c;
+  }
 }
 
 // Stable scatter of one tile, in order, 512 elements at a time.
@@ -232,6 +304,13 @@ bt_scan_rows(const T* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
     int32_t bt[VPL], bd[VPL];
 #pragma unroll
     for (int q = 0; q < VPL; ++q) { bt[q] = kTInf; bd[q] = -1; }
+    // int16 costs: one 32-bit key per column, ((t + 32768) << 16) | row of
+    // the item, so the lexicographic (t, d) minimum is one unsigned min
+    // (rows of an item are in increasing d; t fits 16 bits because costs
+    // are positive int16)
+    uint32_t key[VPL];
+#pragma unroll
+    for (int q = 0; q < VPL; ++q) key[q] = 0xffffffffu;
     if (g < R) {
       // software pipeline: the unit ids of the next U rows are loaded while
       // the current U rows are loaded and reduced.  Rows of a thread arrive
@@ -261,13 +340,38 @@ bt_scan_rows(const T* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
             x[u] = load16(rp + slot * VPL);
           }
         }
+        if constexpr (sizeof(T) == 2) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (d[u] < 0) continue;
+          for (int u = 0; u < U; ++u) {
+            if (d[u] < 0) continue;
+            const uint32_t crow = ((uint32_t)(32768 - own[u]) << 16) | (uint32_t)(p + u * R - r0);
+            const uint4 wv = *reinterpret_cast<const uint4*>(&x[u]);
+            const uint32_t w4[4] = {wv.x, wv.y, wv.z, wv.w};
 #pragma unroll
-          for (int q = 0; q < VPL; ++q) {
-            const int32_t t = (int32_t)x[u].v[q] - own[u];
-            if (t < bt[q]) { bt[q] = t; bd[q] = d[u]; }
+            for (int q = 0; q < 4; ++q) {
+              key[2 * q] = min(key[2 * q], (w4[q] << 16) + crow);
+              key[2 * q + 1] = min(key[2 * q + 1], (w4[q] & 0xffff0000u) + crow);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            if (d[u] < 0) continue;
+#pragma unroll
+            for (int q = 0; q < VPL; ++q) {
+              const int32_t t = (int32_t)x[u].v[q] - own[u];
+              if (t < bt[q]) { bt[q] = t; bd[q] = d[u]; }
+            }
+          }
+        }
+      }
+      if constexpr (sizeof(T) == 2) {
+#pragma unroll
+        for (int q = 0; q < VPL; ++q) {
+          if (key[q] != 0xffffffffu) {
+            bt[q] = (int32_t)(key[q] >> 16) - 32768;
+            bd[q] = (int32_t)min((uint32_t)__ldg(perm + r0 + (int32_t)(key[q] & 0xffffu)),
+                                 (uint32_t)(n - 1));
           }
         }
       }
@@ -329,7 +433,8 @@ cudaError_t best_transfer_run(int32_t n, int32_t k, const void* cm, int elem_byt
   int32_t *sk = W.k0, *sv = W.v0, *dk = W.k1, *dv = W.v1;
   for (int p = 0; p < passes; ++p) {
     bt_hist<<<(unsigned)W.ntiles, kThreads, 0, st>>>(sk, n, 8 * p, W.tile_hist, W.ntiles);
-    bt_scan<<<1, kThreads, 0, st>>>(W.tile_hist, 256 * W.ntiles, nullptr);
+    bt_digit_sums<<<256, kThreads, 0, st>>>(W.tile_hist, W.ntiles, W.dsum);
+    bt_digit_scan<<<256, kThreads, 0, st>>>(W.tile_hist, W.ntiles, W.dsum);
     bt_scatter<<<(unsigned)W.ntiles, kThreads, 0, st>>>(sk, sv, dk, dv, n, 8 * p, W.tile_hist,
                                                         W.ntiles);
     std::swap(sk, dk);
