@@ -58,6 +58,9 @@ def parse():
                     help="rounds of the CPU oracle timed for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-scan", action="store_true")
+    ap.add_argument("--max-rounds", type=int, default=-1,
+                    help="city/tiny, profiling only: stop every solve after this many rounds "
+                         "(the line is then not a full-solve measurement)")
     return ap.parse_args()
 
 
@@ -263,7 +266,7 @@ def run_ours(args):
 
     def step():
         solver.reset()
-        solver.solve()
+        solver.solve(args.max_rounds)
 
     for _ in range(args.warmup):
         step()
@@ -311,7 +314,7 @@ def run_ours(args):
     # slow the rounds, so they are off in the timed steps)
     lb.set_option(solver.h, lb.OPT_PHASE_TIMERS, 1)
     solver.reset()
-    solver.solve()
+    solver.solve(args.max_rounds)
     stp = solver.stats()
     lb.set_option(solver.h, lb.OPT_PHASE_TIMERS, 0)
     assert solver.objective == objective
@@ -330,7 +333,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             h = lb.create(inst.n, inst.k, cm_host.numpy(), inst.cap, inst.pen)
-            lb.solve(h)
+            lb.solve(h, args.max_rounds)
             a = lb.assignment(h, inst.n)
             obj = lb.objective(h)
             lb.destroy(h)
@@ -353,6 +356,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "n": inst.n, "k": inst.k, "seed": inst.recipe.seed,
                        "cluster_size": st1.cluster_size, "objective": objective,
                        "l2": "inputs larger than L2 (200 MB CM)",
+                       "max_rounds": args.max_rounds,
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": steps,
             "clocks": clk, "roofline": roofline, "e2e": e2e, "scan": scan,

@@ -124,6 +124,20 @@ int lbdd_create(lbdd_solver** out, int32_t n, int32_t k, const void* cm, int cm_
 /* Set an lbdd_option; LBDD_ERR_ARG for an unknown option or bad value. */
 int lbdd_set_option(lbdd_solver* s, int option, int64_t value);
 
+/* Create a solver for a strict-LBDD instance (Appendix B, Alg. 5, Theorem 2):
+ * no center may exceed its capacity.  If the capacities sum to less than n,
+ * a dummy center k is added with capacity n - sum(cap) and cost max(CM) + 1
+ * for every unit, so the solver has k + 1 centers and the assignment may use
+ * index k.  lbdd_solve then runs Alg. 5: units in index order, each to the
+ * cheapest center with a vacancy (lowest index on ties), then Negative Cycle
+ * Refinement at that center, where a center with a vacancy can pass a dummy
+ * unit on at cost 0 (its transfer costs are min(T, 0)).  The final allotment
+ * minimises the cost over capacity-respecting allotments of the extended
+ * instance; lbdd_objective returns that cost.  Arguments as lbdd_create,
+ * without penalties.  Errors as lbdd_create. */
+int lbdd_create_strict(lbdd_solver** out, int32_t n, int32_t k, const void* cm, int cm_dtype,
+                       int cm_is_device, const int32_t* cap, void* cuda_stream);
+
 /* Run rounds of Alg. 2 (each: allot the next unit of the MinDistance order
  * to its most suitable center, Negative Cycle Refinement at that center,
  * and Negative Path Refinement if the center was full).  max_rounds < 0

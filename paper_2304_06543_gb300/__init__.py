@@ -19,7 +19,7 @@ import numpy as np
 from . import _build
 
 __all__ = [
-    "load", "LbddError", "Solver", "create", "solve", "reset", "solve_batch", "objective",
+    "load", "LbddError", "Solver", "create", "create_strict", "solve", "reset", "solve_batch", "objective",
     "assignment", "loads", "rounds_done", "get_stats", "best_transfer_table",
     "best_transfer", "best_transfer_workspace", "cm_pitch", "strerror", "destroy",
     "Batch", "autotune", "tune_get", "tune_clear", "Server", "RequestInfo", "ServerStats",
@@ -86,6 +86,7 @@ def load():
                                   ctypes.c_size_t)
         lib.lbdd_create.argtypes = [ctypes.POINTER(P), i32, i32, P, c_int, c_int, P, P, P]
         lib.lbdd_set_option.argtypes = [P, c_int, i64]
+        lib.lbdd_create_strict.argtypes = [ctypes.POINTER(P), i32, i32, P, c_int, c_int, P, P]
         lib.lbdd_solve.argtypes = [P, i64]
         lib.lbdd_reset.argtypes = [P]
         lib.lbdd_solve_batch.argtypes = [ctypes.POINTER(P), c_int, i64, c_int, c_int, P]
@@ -210,6 +211,18 @@ def create(n, k, cm, cap, pen, stream=None, cm_dtype=None):
     return h
 
 
+def create_strict(n, k, cm, cap, stream=None):
+    """lbdd_create_strict (Alg. 5).  cm: numpy (n, k) int32/int16 (host)."""
+    lib = load()
+    cap = np.ascontiguousarray(cap, dtype=np.int32)
+    cm = np.ascontiguousarray(cm)
+    dt = {np.dtype(np.int32): CM_I32, np.dtype(np.int16): CM_I16}[cm.dtype]
+    h = ctypes.c_void_p()
+    _check(lib.lbdd_create_strict(ctypes.byref(h), int(n), int(k), cm.ctypes.data, dt, 0,
+                                  cap.ctypes.data, _stream_handle(stream)), "lbdd_create_strict")
+    return h
+
+
 def set_option(h, option: int, value: int):
     _check(load().lbdd_set_option(h, option, value), "lbdd_set_option")
 
@@ -303,16 +316,22 @@ def destroy(h):
 
 
 class Solver:
-    """RAII wrapper around one lbdd_solver handle."""
+    """RAII wrapper around one lbdd_solver handle (strict=True: Alg. 5, no
+    penalties; the instance gains a dummy center when capacity is short)."""
 
     def __init__(self, cm, cap, pen, stream=None, cluster: int = 0, ncyc_skip: bool = True,
-                 npath_reuse: bool = True, phase_timers: bool = False):
+                 npath_reuse: bool = True, phase_timers: bool = False, strict: bool = False):
         if isinstance(cm, np.ndarray):
             n, k = cm.shape
         else:
             n, k = int(cm.shape[0]), int(cm.shape[1])
         self.n, self.k = int(n), int(k)
-        self.h = create(self.n, self.k, cm, cap, pen, stream=stream)
+        if strict:
+            self.h = create_strict(self.n, self.k, cm, cap, stream=stream)
+            if int(np.sum(np.asarray(cap, dtype=np.int64))) < self.n:
+                self.k += 1
+        else:
+            self.h = create(self.n, self.k, cm, cap, pen, stream=stream)
         if cluster:
             set_option(self.h, OPT_CLUSTER, cluster)
         if not ncyc_skip:

@@ -201,7 +201,14 @@ struct Solver {
     int32_t* keys0 = I.sort_tmp;
     int32_t* vals0 = I.sort_tmp + n;
     uint32_t kmax = 0;
-    for (int64_t d = (int64_t)rank * kWarps + warp; d < n; d += (int64_t)C * kWarps) {
+    const bool strict = flags & OPT_STRICT;
+    if (strict) {   // Alg. 5 visits the units in index order; centers are chosen per round
+      for (int64_t d = (int64_t)rank * kThreads + tid; d < n; d += (int64_t)C * kThreads) {
+        I.order[d] = (int32_t)d;
+        I.assign[d] = -1;
+      }
+    }
+    for (int64_t d = (int64_t)rank * kWarps + warp; d < n && !strict; d += (int64_t)C * kWarps) {
       const T* r = row((int32_t)d);
       int32_t bv = INT32_MAX, bj = INT32_MAX;
       for (int col = lane * VPL; col < k; col += 32 * VPL) {
@@ -239,9 +246,40 @@ struct Solver {
                         (unsigned long long)kmax);
     __syncthreads();
     cluster_sync_all();
-    if (rank == 0) sort_order();
+    if (rank == 0 && !strict) sort_order();
     __syncthreads();
     cluster_sync_all();
+  }
+
+  // Alg. 5: the cheapest center that still has a vacancy (a dummy unit),
+  // lowest index on equal cost; every CTA computes the same answer from the
+  // row and its load/capacity replicas.  -1 if no center has a vacancy.
+  __device__ int32_t strict_target(int32_t d) {
+    const T* r = row(d);
+    int32_t bv = INT32_MAX, bj = -1;
+    for (int s = tid; s < k; s += kThreads) {
+      if (s_load[s] < s_cap[s]) {
+        const int32_t v = (int32_t)r[s];
+        if (v < bv) { bv = v; bj = s; }
+      }
+    }
+    auto better = [](int32_t v, int32_t j, int32_t bv_, int32_t bj_) {
+      return bj_ < 0 || (j >= 0 && (v < bv_ || (v == bv_ && j < bj_)));
+    };
+    for (int off = 16; off > 0; off >>= 1) {
+      const int32_t ov = __shfl_xor_sync(0xffffffffu, bv, off);
+      const int32_t oj = __shfl_xor_sync(0xffffffffu, bj, off);
+      if (better(ov, oj, bv, bj)) { bv = ov; bj = oj; }
+    }
+    int2* part = reinterpret_cast<int2*>(s_red);
+    if ((tid & 31) == 0) part[tid >> 5] = make_int2(bv, bj);
+    __syncthreads();
+    bv = INT32_MAX;
+    bj = -1;
+    for (int w2 = 0; w2 < kWarps; ++w2)
+      if (better(part[w2].x, part[w2].y, bv, bj)) { bv = part[w2].x; bj = part[w2].y; }
+    __syncthreads();   // part is scratch for the next user
+    return bj;
   }
 
   // Stable LSD radix sort of (key, d) by key, by CTA 0 alone.  The values
@@ -428,6 +466,7 @@ struct Solver {
   // entries slice, slice+step, ...  Lanes of a warp hold consecutive owned
   // columns and walk the same frontier entries, so the key read is a
   // broadcast and the cost reads are consecutive (no bank conflicts).
+  template <bool STRICT>
   __device__ __forceinline__ uint64_t relax_column(int cl, bool valid, int slice, int step,
                                                    int nfront, int32_t j, bool npath,
                                                    int32_t pen_j) const {
@@ -457,23 +496,33 @@ struct Solver {
 #pragma unroll
         for (int q = 0; q < U; ++q) t[q] = (int32_t)col[(int32_t)(key[q] & 0xffffu) * ws];
 #pragma unroll
-        for (int q = 0; q < U; ++q)
+        for (int q = 0; q < U; ++q) {
+          if (STRICT) t[q] = strict_cost(t[q], (int32_t)(key[q] & 0xffffu), kTsInf);
           if (t[q] != kTsInf) best = min(best, key[q] + ((uint64_t)(int64_t)t[q] << 16));
+        }
       }
       for (; f < nfront; f += step) {
         const uint64_t key = s_front[f];
-        const int32_t t = (int32_t)col[(int32_t)(key & 0xffffu) * ws];
+        int32_t t = (int32_t)col[(int32_t)(key & 0xffffu) * ws];
+        if (STRICT) t = strict_cost(t, (int32_t)(key & 0xffffu), kTsInf);
         if (t != kTsInf) best = min(best, key + ((uint64_t)(int64_t)t << 16));
       }
     } else {
       const int32_t* col = I.tc + c0 + cl;
       for (; f < nfront; f += step) {
         const uint64_t key = s_front[f];
-        const int32_t t = col[(int64_t)(key & 0xffffu) * k];
+        int32_t t = col[(int64_t)(key & 0xffffu) * k];
+        if (STRICT) t = strict_cost(t, (int32_t)(key & 0xffffu), kTInf);
         if (t != kTInf) best = min(best, key + ((uint64_t)(int64_t)t << 16));
       }
     }
     return best;
+  }
+
+  // Alg. 5 edge cost: a center with a vacancy can pass a dummy unit on for
+  // free, so its transfer costs are min(T, 0) (an absent edge becomes 0).
+  __device__ __forceinline__ int32_t strict_cost(int32_t t, int32_t u, int32_t inf) const {
+    return (t == inf || t > 0) && s_load[u] < s_cap[u] ? 0 : t;
   }
 
   // Strict improvement of owned column cl.  Returns the frontier key to
@@ -533,6 +582,7 @@ struct Solver {
     const int owner_j = j / w;
     const int32_t pen_j = __ldg(I.pen + j);
     const int obs = w + (int)kOutboxExtra;
+    const bool strict = flags & OPT_STRICT;
     // lanes own 32 consecutive columns (a column block); the WPB warps of a
     // block split the frontier and their minima are combined in shared memory
     const int CB = max(1, (wr + 31) / 32);
@@ -561,8 +611,9 @@ struct Solver {
         const int blk = warp / WPB, slice = warp % WPB;
         if (blk < CB) {
           const int cl = blk * 32 + lane;
-          red_k[slice * CB * 32 + cl] = relax_column(cl, cl < wr, slice, WPB, nfront, j, npath,
-                                                     pen_j);
+          red_k[slice * CB * 32 + cl] =
+              strict ? relax_column<true>(cl, cl < wr, slice, WPB, nfront, j, npath, pen_j)
+                     : relax_column<false>(cl, cl < wr, slice, WPB, nfront, j, npath, pen_j);
         }
         __syncthreads();
         if (timer()) B->t_rloop += clock_cycles() - t0;
@@ -578,7 +629,9 @@ struct Solver {
       } else {
         for (int blk = warp; blk < CB; blk += kWarps) {
           const int cl = blk * 32 + lane;
-          const uint64_t best = relax_column(cl, cl < wr, 0, 1, nfront, j, npath, pen_j);
+          const uint64_t best =
+              strict ? relax_column<true>(cl, cl < wr, 0, 1, nfront, j, npath, pen_j)
+                     : relax_column<false>(cl, cl < wr, 0, 1, nfront, j, npath, pen_j);
           if (cl < w) ob[cl] = cl < wr ? record(cl, best, j, sink_dist, sweep, ob) : kNoKey;
         }
         for (int cl = CB * 32 + tid; cl < w; cl += kThreads) ob[cl] = kNoKey;
@@ -751,11 +804,16 @@ struct Solver {
     if (tid < 32) {
       // every CTA reads the moved units (T is not written before the
       // barrier below, so all CTAs see the same entries)
+      const bool strict = flags & OPT_STRICT;
       for (int i = tid; i < m; i += 32) {
         const int32_t from = s_path[i];
         const int32_t to = (i + 1 < m) ? s_path[i + 1] : (npath ? -1 : j);
         int32_t x = to >= 0 ? __ldcg(I.td + (int64_t)from * k + to) : -1;
-        if (to >= 0 && (uint32_t)x >= (uint32_t)n) { x = -1; if (rank == 0) B->err0 = ST_ERR_INVARIANT; }
+        // Alg. 5: a dummy unit moves where the edge cost came from a vacancy
+        const bool dummy = strict && to >= 0 && s_load[from] < s_cap[from] &&
+                           __ldcg(I.tc + (int64_t)from * k + to) > 0;
+        if (dummy) x = -1;
+        else if (to >= 0 && (uint32_t)x >= (uint32_t)n) { x = -1; if (rank == 0) B->err0 = ST_ERR_INVARIANT; }
         s_pathu[i] = x;
       }
       __syncwarp();
@@ -778,6 +836,21 @@ struct Solver {
         if (x_out >= 0) I.assign[x_out] = (i + 1 < m) ? s_path[i + 1] : j;
       }
       __syncwarp();
+      if (lane == 0 && (flags & OPT_STRICT)) {
+        // centers that only lose or only gain a real unit (the other side of
+        // their edge pair is a dummy); pages are shared, so one thread
+        for (int i = 0; i < m; ++i) {
+          const int32_t c = s_path[i];
+          const int32_t x_out = s_pathu[i], x_in = s_pathu[i > 0 ? i - 1 : m - 1];
+          if (x_out >= 0 && x_in < 0) {
+            list_remove_at(c, ppos[i]);
+            I.load[c] -= 1;
+          } else if (x_out < 0 && x_in >= 0) {
+            list_append(c, x_in);
+            I.load[c] += 1;
+          }
+        }
+      }
       if (lane == 0) {
         if (npath) {
           // the anchor loses x_0, the terminal center gains x_{m-2}
@@ -798,6 +871,13 @@ struct Solver {
     if (npath && tid == 0) {   // load replicas in every CTA
       s_load[j] -= 1;
       s_load[s_path[m - 1]] += 1;
+    }
+    if ((flags & OPT_STRICT) && tid == 0) {
+      for (int i = 0; i < m; ++i) {
+        const int32_t x_out = s_pathu[i], x_in = s_pathu[i > 0 ? i - 1 : m - 1];
+        if (x_out >= 0 && x_in < 0) s_load[s_path[i]] -= 1;
+        else if (x_out < 0 && x_in >= 0) s_load[s_path[i]] += 1;
+      }
     }
     __syncthreads();
     cluster_sync_all();   // member lists updated before anyone rescans
@@ -929,9 +1009,10 @@ struct Solver {
       const uint64_t tm0 = timer() ? clock_cycles() : 0;
       const int32_t d = __ldcg(I.order + r);
       if ((uint32_t)d >= (uint32_t)n) { status = ST_ERR_INVARIANT; break; }   // uniform guard
-      const int32_t j = __ldcg(I.smin + d);
+      const bool strict = flags & OPT_STRICT;
+      const int32_t j = strict ? strict_target(d) : __ldcg(I.smin + d);
       if ((uint32_t)j >= (uint32_t)k) { status = ST_ERR_INVARIANT; break; }
-      const bool over = s_load[j] >= __ldg(I.cap + j);
+      const bool over = !strict && s_load[j] >= __ldg(I.cap + j);
       const bool merged = merge_row(d, j);
       if (tid == 0) s_load[j] += 1;
       if (rank == 0 && tid == 0) {

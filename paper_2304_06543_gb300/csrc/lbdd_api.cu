@@ -278,6 +278,81 @@ extern "C" int lbdd_create(lbdd_solver** out, int32_t n, int32_t k, const void* 
   return create_impl(out, n, k, cm, cm_dtype, cm_is_device, k, cap, pen, cuda_stream);
 }
 
+// Extended cost matrix of Alg. 5: the caller's n x k costs widened to int32,
+// plus (when K > k) a dummy center whose cost is max + 1 for every unit.
+__global__ void strict_extend(const void* cm, int elem, int32_t n, int32_t k, int32_t K,
+                              int32_t fill, int32_t* out) {
+  const int64_t total = (int64_t)n * K;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = i / K, c = i - d * K;
+    out[i] = c < k ? (elem == 2 ? (int32_t)static_cast<const int16_t*>(cm)[d * k + c]
+                                : static_cast<const int32_t*>(cm)[d * k + c])
+                   : fill;
+  }
+}
+
+extern "C" int lbdd_create_strict(lbdd_solver** out, int32_t n, int32_t k, const void* cm,
+                                  int cm_dtype, int cm_is_device, const int32_t* cap,
+                                  void* cuda_stream) {
+  if (!out) return LBDD_ERR_ARG;
+  *out = nullptr;
+  if (n < 1 || k < 1 || k > 65534 || !cm || !cap) return LBDD_ERR_ARG;
+  if (cm_dtype != LBDD_CM_I32 && cm_dtype != LBDD_CM_I16) return LBDD_ERR_ARG;
+  int64_t capsum = 0;
+  for (int32_t i = 0; i < k; ++i) {
+    if (cap[i] < 1) return LBDD_ERR_ARG;
+    capsum += cap[i];
+  }
+  const int32_t K = capsum < n ? k + 1 : k;
+  int dev = 0, sms = 0;
+  int rc = check_device(&dev, &sms);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int elem = cm_dtype == LBDD_CM_I16 ? 2 : 4;
+  const size_t in_bytes = (size_t)n * k * elem;
+  void* src = nullptr;
+  int32_t* ext = nullptr;
+  int* mm = nullptr;
+  auto cleanup = [&]() {
+    if (src && !cm_is_device) cudaFreeAsync(src, st);
+    if (ext) cudaFreeAsync(ext, st);
+    if (mm) cudaFreeAsync(mm, st);
+    cudaStreamSynchronize(st);
+  };
+  cudaError_t e = cudaSuccess;
+  if (cm_is_device) {
+    src = const_cast<void*>(cm);
+  } else {
+    e = cudaMallocAsync(&src, in_bytes, st);
+    if (!e) e = cudaMemcpyAsync(src, cm, in_bytes, cudaMemcpyHostToDevice, st);
+  }
+  if (!e) e = cudaMallocAsync(reinterpret_cast<void**>(&ext), 4ull * n * K, st);
+  if (!e) e = cudaMallocAsync(reinterpret_cast<void**>(&mm), 2 * sizeof(int), st);
+  int res[2] = {INT32_MAX, INT32_MIN};
+  if (!e) e = cudaMemcpyAsync(mm, res, sizeof(res), cudaMemcpyHostToDevice, st);
+  if (!e) {
+    cm_minmax<<<sms * 4, 256, 0, st>>>(src, elem, k, n, k, mm, mm + 1);
+    e = cudaGetLastError();
+  }
+  if (!e) e = cudaMemcpyAsync(res, mm, sizeof(res), cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  if (e) { rc = cuda_fail(e, "lbdd_create_strict"); cleanup(); return rc; }
+  if (res[0] < 1 || res[1] == INT32_MAX) { cleanup(); return LBDD_ERR_ARG; }
+  strict_extend<<<sms * 8, 256, 0, st>>>(src, elem, n, k, K, res[1] + 1, ext);
+  e = cudaGetLastError();
+  if (e) { rc = cuda_fail(e, "strict_extend"); cleanup(); return rc; }
+  std::vector<int32_t> capx(cap, cap + k), penx(K, 1);
+  if (K > k) capx.push_back((int32_t)(n - capsum));
+  lbdd_solver* s = nullptr;
+  rc = create_impl(&s, n, K, ext, LBDD_CM_I32, 1, K, capx.data(), penx.data(), cuda_stream);
+  cleanup();
+  if (rc) return rc;
+  s->strict = 1;
+  *out = s;
+  return LBDD_OK;
+}
+
 int lbdd::clone_solver(const lbdd_solver* src, lbdd_solver** out) {
   std::vector<int32_t> cap(src->k), pen(src->k);
   CK(cudaMemcpyAsync(cap.data(), src->cap, 4ull * src->k, cudaMemcpyDeviceToHost, src->st));
@@ -338,7 +413,8 @@ static int set_target(lbdd_solver* s, int64_t max_rounds, cudaStream_t st) {
 
 int lbdd::solver_flags(const lbdd_solver* s) {
   return (s->ncyc_skip ? 0 : OPT_NO_NCYC_SKIP) | (s->npath_reuse ? 0 : OPT_NO_NPATH_REUSE) |
-         (s->tc_smem ? 0 : OPT_NO_TC_SMEM) | (s->phase_timers ? OPT_PHASE_TIMERS : 0);
+         (s->tc_smem ? 0 : OPT_NO_TC_SMEM) | (s->phase_timers ? OPT_PHASE_TIMERS : 0) |
+         (s->strict ? OPT_STRICT : 0);
 }
 
 int lbdd::choose_cluster(lbdd_solver* s) {

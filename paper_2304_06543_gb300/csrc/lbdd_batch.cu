@@ -178,19 +178,20 @@ static int make_plan(lbdd_solver* const* v, const int64_t* rem, int m, int force
   for (int i = 0; i < m; ++i) {
     (*cluster_of)[i] = est[i].C;
     Group* g = nullptr;
+    const int fl = solver_flags(v[i]);
     for (auto& x : *groups)
-      if (x.elem == v[i]->elem && x.C == est[i].C) g = &x;
+      if (x.elem == v[i]->elem && x.C == est[i].C && x.flags == fl) g = &x;
     if (!g) {
       groups->push_back(Group{});
       g = &groups->back();
       g->elem = v[i]->elem;
       g->C = est[i].C;
+      g->flags = fl;
     }
     g->idx.push_back(i);
     const double len = (double)rem[i] * est[i].t;
     g->work += len * est[i].C;
     g->longest = std::max(g->longest, len);
-    g->flags |= solver_flags(v[i]);
   }
   // heaviest group first; inside a group, longest instance first
   std::stable_sort(groups->begin(), groups->end(),
@@ -249,7 +250,7 @@ static int make_plan(lbdd_solver* const* v, const int64_t* rem, int m, int force
 
 // ----------------------------------------------------------- the batch ---
 
-constexpr int kMaxGroups = 2 * kNC;     // one per (cost width, cluster size)
+constexpr int kMaxGroups = 16;          // one per (cost width, cluster size, solver options)
 
 struct lbdd_batch {
   int capacity = 0;                 // instances the buffers hold
@@ -371,6 +372,7 @@ int batch_set(lbdd_batch* b, lbdd_solver* const* solvers, const int64_t* rem, in
   int rc = make_plan(solvers, r.data(), m, cluster_size, max_clusters, b->dev, b->sms,
                      shortest_first ? SHORTEST_FIRST : LONGEST_FIRST, &b->groups, &b->cluster_of);
   if (rc) return rc;
+  if (b->groups.size() > (size_t)kMaxGroups) return LBDD_ERR_ARG;
   b->slot_of.assign(m, 0);
   b->offset.clear();
   int pos = 0;

@@ -67,6 +67,7 @@ enum : int {
   OPT_NO_NPATH_REUSE = 2, // always run the NegPath Bellman-Ford
   OPT_NO_TC_SMEM = 4,     // keep the owned cost slice in global memory only
   OPT_PHASE_TIMERS = 8,   // time the phases of every round (CTA 0, thread 0)
+  OPT_STRICT = 32,        // strict-LBDD (Alg. 5): vacancies as zero-cost dummy units
 };
 
 // Device view of one instance.  Pointers are device memory owned by the

@@ -47,6 +47,7 @@ struct lbdd_solver {
   int npath_reuse = 1;
   int tc_smem = 1;
   int phase_timers = 0;
+  int strict = 0;          // strict-LBDD instance (Alg. 5), k includes a dummy center if any
   int device = 0;
   int num_sms = 0;
   size_t bytes = 0;        // device bytes held now
