@@ -225,6 +225,22 @@ def make_named(name: str, dtype: str = "i32", **overrides) -> Instance:
     return make(r, dtype=dtype)
 
 
+def penalty_table(seed: int, k: int, Q: int, base=(1, 30), step=(0, 10)) -> np.ndarray:
+    """General penalty functions (Def. 4) as a k x Q table: q_s(j) for the
+    j-th allotment beyond capacity, j = 1..Q (the last value repeats).
+    q_s(1) uniform in `base`, then non-decreasing by steps uniform in `step`;
+    drawn from the counter stream of `seed`."""
+    lib = _load()
+    q = np.empty((k, Q), dtype=np.int32)
+    for s in range(k):
+        v = base[0] + int(lib.lbdd_gen_u64(seed, 60, s) % (base[1] - base[0] + 1))
+        for j in range(Q):
+            if j:
+                v += step[0] + int(lib.lbdd_gen_u64(seed, 61, s * Q + j) % (step[1] - step[0] + 1))
+            q[s, j] = v
+    return q
+
+
 def random_small(seed: int, n: int, k: int, cm_max: int = 20, cap_frac: float = 0.7,
                  pen=(1, 30)) -> Instance:
     """Tiny instance with CM uniform in [1, cm_max] drawn from the counter

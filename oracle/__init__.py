@@ -54,6 +54,9 @@ def _load():
         lib.oracle_bf.argtypes = [i64, i64, P, P, P, P]
         lib.oracle_has_negative_cycle.argtypes = [i64, P]
         lib.oracle_asral.argtypes = [i64, i64, P, P, P, c_int, i64, c_int, P, P, P, P]
+        lib.oracle_asral_q.argtypes = [i64, i64, P, P, P, i64, c_int, i64, c_int, P, P, P, P]
+        lib.oracle_objective_q.argtypes = [i64, i64, P, P, P, i64, P]
+        lib.oracle_objective_q.restype = i64
         lib.oracle_strict.argtypes = [i64, i64, P, P, P, P, P]
         _lib = lib
     return _lib
@@ -137,6 +140,33 @@ def asral(cm, cap, pen, mode=MODE_HEAP, max_rounds=-1, check=False) -> Result:
     rc = _load().oracle_asral(n, k, _p(cm), _p(cap), _p(pen), int(mode), int(max_rounds),
                               int(bool(check)), _p(assign), _p(load), ctypes.byref(delta),
                               ctypes.byref(st))
+    stats = {f: getattr(st, f) for f, _ in _Stats._fields_}
+    return Result(assign=assign, load=load, delta=int(delta.value), stats=stats, rc=rc)
+
+
+def objective_q(cm, cap, qtab, assign) -> int:
+    """Eq. (1) with penalty tables qtab (k x Q): q_s(j) = qtab[s, min(j, Q) - 1]."""
+    cm = _c(cm, np.int32)
+    n, k = cm.shape
+    qtab = _c(qtab, np.int32)
+    return int(_load().oracle_objective_q(n, k, _p(cm), _p(_c(cap, np.int32)), _p(qtab),
+                                          qtab.shape[1], _p(_c(assign, np.int32))))
+
+
+def asral_q(cm, cap, qtab, mode=MODE_HEAP, max_rounds=-1, check=False) -> Result:
+    """Alg. 2 with general penalty functions (Def. 4) given as tables (k x Q)."""
+    cm = _c(cm, np.int32)
+    n, k = cm.shape
+    cap = _c(cap, np.int32)
+    qtab = _c(qtab, np.int32)
+    assert qtab.ndim == 2 and qtab.shape[0] == k
+    assign = np.empty(n, np.int32)
+    load = np.empty(k, np.int64)
+    delta = ctypes.c_int64(0)
+    st = _Stats()
+    rc = _load().oracle_asral_q(n, k, _p(cm), _p(cap), _p(qtab), qtab.shape[1], int(mode),
+                                int(max_rounds), int(bool(check)), _p(assign), _p(load),
+                                ctypes.byref(delta), ctypes.byref(st))
     stats = {f: getattr(st, f) for f, _ in _Stats._fields_}
     return Result(assign=assign, load=load, delta=int(delta.value), stats=stats, rc=rc)
 

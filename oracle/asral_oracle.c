@@ -8,9 +8,12 @@
  * and the CPU-baseline leg of the benchmark may load it.
  *
  * Everything is integer.  CM entries are positive integers (Table 1, Def. of
- * the cost matrix), capacities positive integers, and the penalty of a center
- * is the constant per-unit form used in the experiments (Section 5): the
- * j-th unit beyond capacity costs pen[s] for every j >= 1.
+ * the cost matrix), capacities positive integers.  The penalty function of a
+ * center (Def. 4) returns the extra cost of the j-th allotment beyond
+ * capacity, q_s(j) > 0, non-decreasing in j.  It is given as a table of Q
+ * values per center, q_s(j) = qtab[s*Q + min(j, Q) - 1] (the last value
+ * repeats); Q = 1 is the constant per-unit form of the experiments
+ * (Section 5), where pen[s] is the table.
  *
  * Readings where the paper is silent or loose (all documented in DESIGN):
  *  - "ties are broken arbitrarily" (Defs. 9 and 10): the best-transfer edge
@@ -29,8 +32,10 @@
  *    the extra "cost of last edge" update of Alg. 4): the objective changes by the
  *    path cost exactly once (transfer edges CM(new) - CM(old), plus the
  *    penalty edge for a negative path);
- *  - Def. 10 (c): q_u() is pen[u] when u is at or above capacity, else 0;
- *    q_{s*}() is pen[s*] (s* is over capacity whenever Alg. 4 runs).
+ *  - Def. 10 (c): q_u() is the penalty one more unit would pay at u, i.e.
+ *    q_u(load_u - c_u + 1) when u is at or above capacity, else 0; q_{s*}()
+ *    is the penalty the anchor's last unit beyond capacity paid,
+ *    q_{s*}(load - c) (s* is over capacity whenever Alg. 4 runs).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -56,13 +61,18 @@ typedef struct {
     int64_t moves;
 } oracle_stats;
 
+/* q_s(j), j >= 1: penalty of the j-th allotment beyond capacity (Def. 4). */
+static int64_t q_of(const int32_t *qtab, int64_t Q, int64_t s, int64_t j) {
+    return qtab[s * Q + (j < Q ? j : Q) - 1];
+}
+
 /* ------------------------------------------------------------------------
- * Objective, Eq. (1): sum of CM over the allotment plus the total penalty.
- * With a constant per-unit penalty, center s pays pen[s] * max(0, load-cap).
+ * Objective, Eq. (1): sum of CM over the allotment plus the total penalty,
+ * center s paying q_s(1) + ... + q_s(load - cap) when load > cap.
  * Units with assign[d] < 0 are not allotted and contribute nothing.
  */
-int64_t oracle_objective(int64_t n, int64_t k, const int32_t *cm, const int32_t *cap,
-                         const int32_t *pen, const int32_t *assign) {
+int64_t oracle_objective_q(int64_t n, int64_t k, const int32_t *cm, const int32_t *cap,
+                           const int32_t *qtab, int64_t Q, const int32_t *assign) {
     int64_t total = 0;
     int64_t *load = (int64_t *)calloc((size_t)k, sizeof(int64_t));
     if (!load) return INT64_MIN;
@@ -73,9 +83,14 @@ int64_t oracle_objective(int64_t n, int64_t k, const int32_t *cm, const int32_t 
         load[a] += 1;
     }
     for (int64_t s = 0; s < k; ++s)
-        if (load[s] > cap[s]) total += (int64_t)pen[s] * (load[s] - cap[s]);
+        for (int64_t j = 1; j <= load[s] - cap[s]; ++j) total += q_of(qtab, Q, s, j);
     free(load);
     return total;
+}
+
+int64_t oracle_objective(int64_t n, int64_t k, const int32_t *cm, const int32_t *cap,
+                         const int32_t *pen, const int32_t *assign) {
+    return oracle_objective_q(n, k, cm, cap, pen, 1, assign);
 }
 
 /* ------------------------------------------------------------------------
@@ -238,7 +253,8 @@ static void heap_pop(heap64 *h) {
  */
 typedef struct {
     int64_t n, k;
-    const int32_t *cm, *cap, *pen;
+    const int32_t *cm, *cap, *qtab;
+    int64_t Q;
     int mode;
     int32_t *assign;
     int64_t *load;
@@ -310,8 +326,9 @@ static void build_ncyc(asral *S, int32_t j) {
 
 /* NegPath graph NPath(Gamma(B3), j), Def. 10.  Transfer edges as in (a)/(b);
  * (c) u -> s*in costs q_u() - q_{s*}(): the penalty of one more unit at u
- * (pen[u] if u is at or above capacity, else 0) minus the penalty saved at
- * the overloaded anchor (pen[j]); (d) self loops cost 0 and are omitted
+ * (q_u(load_u - c_u + 1) if u is at or above capacity, else 0) minus the
+ * penalty saved at the overloaded anchor, q_j(load_j - c_j), the penalty of
+ * its last unit beyond capacity; (d) self loops cost 0 and are omitted
  * because a 0-cost loop never shortens a path. */
 static void build_npath(asral *S, int32_t j) {
     int64_t k = S->k, N = k + 1;
@@ -322,8 +339,9 @@ static void build_npath(asral *S, int32_t j) {
             S->W[u * N + v] = S->tc[u * k + v];
         }
         if (u != j) {
-            int64_t qu = S->load[u] >= S->cap[u] ? S->pen[u] : 0;
-            S->W[u * N + k] = qu - (int64_t)S->pen[j];
+            int64_t qu = S->load[u] >= S->cap[u]
+                             ? q_of(S->qtab, S->Q, u, S->load[u] - S->cap[u] + 1) : 0;
+            S->W[u * N + k] = qu - q_of(S->qtab, S->Q, j, S->load[j] - S->cap[j]);
         }
     }
 }
@@ -458,9 +476,9 @@ int oracle_has_negative_cycle(int64_t k, const int64_t *tc) {
 }
 
 static int asral_init(asral *S, int64_t n, int64_t k, const int32_t *cm, const int32_t *cap,
-                      const int32_t *pen, int mode, int32_t *assign) {
+                      const int32_t *qtab, int64_t Q, int mode, int32_t *assign) {
     memset(S, 0, sizeof(*S));
-    S->n = n; S->k = k; S->cm = cm; S->cap = cap; S->pen = pen; S->mode = mode;
+    S->n = n; S->k = k; S->cm = cm; S->cap = cap; S->qtab = qtab; S->Q = Q; S->mode = mode;
     S->assign = assign;
     int64_t N = k + 1;
     S->load = (int64_t *)calloc((size_t)k, sizeof(int64_t));
@@ -492,7 +510,7 @@ static void asral_free(asral *S) {
 /* ------------------------------------------------------------------------
  * Alg. 2 (ASRAL).  Runs `max_rounds` rounds (or all n if max_rounds < 0) of:
  * extract the next unit from the MinDistance order, allot it to its most
- * suitable center j (paying pen[j] if j had no vacancy), Negative Cycle
+ * suitable center j (paying q_j(load - c + 1) if j had no vacancy), Negative Cycle
  * Refinement at j, and, if the allotment overloaded j, Negative Path
  * Refinement at j.
  *   mode: 0 = best-transfer table recomputed by definition every time,
@@ -501,16 +519,20 @@ static void asral_free(asral *S) {
  *          cycle in Gamma) and the incremental objective against Eq. (1).
  * Outputs assign[n] (-1 = not yet allotted), load[k], *delta, *stats.
  */
-int oracle_asral(int64_t n, int64_t k, const int32_t *cm, const int32_t *cap,
-                 const int32_t *pen, int mode, int64_t max_rounds, int check, int32_t *assign,
-                 int64_t *load_out, int64_t *delta_out, oracle_stats *stats) {
-    if (n < 1 || k < 1 || !cm || !cap || !pen || !assign) return OR_ERR_ARG;
-    for (int64_t s = 0; s < k; ++s)
-        if (cap[s] < 1 || pen[s] < 1) return OR_ERR_ARG;
+int oracle_asral_q(int64_t n, int64_t k, const int32_t *cm, const int32_t *cap,
+                   const int32_t *qtab, int64_t Q, int mode, int64_t max_rounds, int check,
+                   int32_t *assign, int64_t *load_out, int64_t *delta_out, oracle_stats *stats) {
+    if (n < 1 || k < 1 || Q < 1 || !cm || !cap || !qtab || !assign) return OR_ERR_ARG;
+    for (int64_t s = 0; s < k; ++s) {
+        if (cap[s] < 1) return OR_ERR_ARG;
+        for (int64_t j = 0; j < Q; ++j)   /* positive and non-decreasing (Def. 4) */
+            if (qtab[s * Q + j] < 1 || (j > 0 && qtab[s * Q + j] < qtab[s * Q + j - 1]))
+                return OR_ERR_ARG;
+    }
     for (int64_t i = 0; i < n * k; ++i)
         if (cm[i] < 1) return OR_ERR_ARG;
     asral S;
-    int rc = asral_init(&S, n, k, cm, cap, pen, mode, assign);
+    int rc = asral_init(&S, n, k, cm, cap, qtab, Q, mode, assign);
     int32_t *smin = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     if (rc == OR_OK && (!smin || !order)) rc = OR_ERR_OOM;
@@ -520,9 +542,10 @@ int oracle_asral(int64_t n, int64_t k, const int32_t *cm, const int32_t *cap,
         int32_t d = order[r];
         int32_t j = smin[d];
         int over = S.load[j] >= cap[j]; /* no vacancy at j */
+        int64_t q = over ? q_of(qtab, Q, j, S.load[j] - cap[j] + 1) : 0;
         assign[d] = j;
         S.load[j] += 1;
-        S.delta += (int64_t)cm[(int64_t)d * k + j] + (over ? (int64_t)pen[j] : 0);
+        S.delta += (int64_t)cm[(int64_t)d * k + j] + q;
         if (mode == MODE_HEAP) rc = heap_add_unit(&S, d, j);
         if (rc == OR_OK) rc = negcycle_refine(&S, j);
         if (rc == OR_OK && over) rc = negpath_refine(&S, j);
@@ -530,7 +553,7 @@ int oracle_asral(int64_t n, int64_t k, const int32_t *cm, const int32_t *cap,
         if (rc == OR_OK && check) {
             rc = oracle_best_transfer(n, k, cm, assign, S.tc, S.td);
             if (rc == OR_OK && oracle_has_negative_cycle(k, S.tc) != 0) rc = OR_ERR_INVARIANT;
-            if (rc == OR_OK && oracle_objective(n, k, cm, cap, pen, assign) != S.delta)
+            if (rc == OR_OK && oracle_objective_q(n, k, cm, cap, qtab, Q, assign) != S.delta)
                 rc = OR_ERR_INVARIANT;
         }
     }
@@ -542,6 +565,15 @@ int oracle_asral(int64_t n, int64_t k, const int32_t *cm, const int32_t *cap,
     free(order);
     asral_free(&S);
     return rc;
+}
+
+/* Alg. 2 with the constant per-unit penalty pen[s] of the experiments. */
+int oracle_asral(int64_t n, int64_t k, const int32_t *cm, const int32_t *cap,
+                 const int32_t *pen, int mode, int64_t max_rounds, int check, int32_t *assign,
+                 int64_t *load_out, int64_t *delta_out, oracle_stats *stats) {
+    if (!pen) return OR_ERR_ARG;
+    return oracle_asral_q(n, k, cm, cap, pen, 1, mode, max_rounds, check, assign, load_out,
+                          delta_out, stats);
 }
 
 /* ------------------------------------------------------------------------

@@ -220,11 +220,12 @@ def test_strict_lbdd_is_optimal():
 _SRC = os.path.join(os.path.dirname(oracle.__file__), "asral_oracle.c")
 
 MUTATIONS = {
-    "dropped_penalty_term": ("(over ? (int64_t)pen[j] : 0)", "0"),
+    "dropped_penalty_term": ("int64_t q = over ? q_of(qtab, Q, j, S.load[j] - cap[j] + 1) : 0;",
+                             "int64_t q = 0;"),
     "transfer_sign": ("int64_t t = (int64_t)cm[d * k + v] - (int64_t)cm[d * k + u];",
                       "int64_t t = (int64_t)cm[d * k + u] - (int64_t)cm[d * k + v];"),
-    "penalty_edge_sign": ("S->W[u * N + k] = qu - (int64_t)S->pen[j];",
-                          "S->W[u * N + k] = (int64_t)S->pen[j] - qu;"),
+    "penalty_edge_sign": ("S->W[u * N + k] = qu - q_of(S->qtab, S->Q, j, S->load[j] - S->cap[j]);",
+                          "S->W[u * N + k] = q_of(S->qtab, S->Q, j, S->load[j] - S->cap[j]) - qu;"),
     "transposed_sink_edge": ("if (u != j) S->W[u * N + k] = S->tc[u * k + j];",
                              "if (u != j) S->W[u * N + k] = S->tc[j * k + u];"),
     "wrong_vacancy_test": ("int over = S.load[j] >= cap[j];", "int over = S.load[j] > cap[j];"),
@@ -269,5 +270,99 @@ def test_planted_mistake_is_caught(name, tmp_path):
         if results[0][3] != results[1][3] or not np.array_equal(results[0][1], results[1][1]):
             caught = True
         if caught:
+            break
+    assert caught, f"mutation {name} escaped every pin"
+
+
+# ------------------------------------------- general penalty functions --
+
+def _qinst(seed, n, k, Q, **kw):
+    J = small(seed, n, k, **kw)
+    return J, L.penalty_table(seed, k, Q, base=(1, 12), step=(0, 9))
+
+
+def test_penalty_table_brute_force_equals_matching_reduction():
+    """The slot reduction with the j-th overload slot at CM + q_s(j) solves
+    Eq. (1) exactly for non-decreasing q (Def. 4)."""
+    for s in range(20):
+        J, q = _qinst(3100 + s, 7, 3, 4, cm_max=9, cap_frac=0.4)
+        assert exact.brute_force_q(J.cm, J.cap, q) == exact.matching_optimum_q(J.cm, J.cap, q)
+
+
+@pytest.mark.parametrize("mode", [oracle.MODE_DEFINITION, oracle.MODE_HEAP])
+def test_asral_with_penalty_tables_against_optimum(mode):
+    """ASRAL with increasing penalties: a feasible value (never below the
+    optimum), the incremental objective equals Eq. (1) and Lemmas 1/2 hold
+    every round (check mode), and the value equals the optimum on every
+    seeded instance here (the penalties are convex)."""
+    for s in range(30):
+        n = [10, 24, 50][s % 3]
+        k = [2, 3, 5][s % 3]
+        J, q = _qinst(3300 + s, n, k, [2, 5, 9][s % 3], cm_max=[6, 25][s % 2],
+                      cap_frac=[0.3, 0.6][s % 2])
+        r = oracle.asral_q(J.cm, J.cap, q, mode=mode, check=True)
+        assert r.rc == oracle.OK
+        assert r.delta == exact.eq1_objective_q(J.cm, J.cap, q, r.assign)
+        opt = exact.matching_optimum_q(J.cm, J.cap, q)
+        assert r.delta >= opt
+        assert r.delta == opt, (s, r.delta, opt)
+
+
+def test_constant_table_equals_constant_penalty():
+    for s in range(8):
+        J = small(3500 + s, 40, 4, cm_max=15, cap_frac=0.5, pen=(1, 30))
+        q = np.repeat(J.pen[:, None], 3, axis=1)
+        a, b = oracle.asral(J.cm, J.cap, J.pen), oracle.asral_q(J.cm, J.cap, q)
+        assert a.delta == b.delta and np.array_equal(a.assign, b.assign)
+
+
+def test_penalty_table_rejects_decreasing_or_nonpositive():
+    J = small(3600, 10, 2)
+    bad = np.array([[5, 4], [1, 1]], np.int32)
+    assert oracle.asral_q(J.cm, J.cap, bad).rc == oracle.ERR_ARG
+    assert oracle.asral_q(J.cm, J.cap, np.array([[1, 2], [0, 1]], np.int32)).rc == oracle.ERR_ARG
+
+
+Q_MUTATIONS = {
+    # the allotment pays the penalty of the previous overload unit
+    "allot_penalty_index": ("int64_t q = over ? q_of(qtab, Q, j, S.load[j] - cap[j] + 1) : 0;",
+                            "int64_t q = over ? q_of(qtab, Q, j, S.load[j] - cap[j] + (S.load[j] > cap[j] ? 0 : 1)) : 0;"),
+    # the penalty edge saves the anchor's next unit instead of its last one
+    "anchor_penalty_index": ("qu - q_of(S->qtab, S->Q, j, S->load[j] - S->cap[j]);",
+                             "qu - q_of(S->qtab, S->Q, j, S->load[j] - S->cap[j] + 1);"),
+    # Eq. (1) charges every overload unit the first table value
+    "objective_flat_table": ("total += q_of(qtab, Q, s, j);", "total += q_of(qtab, Q, s, 1);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(Q_MUTATIONS))
+def test_planted_penalty_table_mistake_is_caught(name, tmp_path):
+    old, new = Q_MUTATIONS[name]
+    src = open(_SRC).read()
+    assert src.count(old) == 1, name
+    mutated = tmp_path / "mut.c"
+    mutated.write_text(src.replace(old, new))
+    so = tmp_path / "mut.so"
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", str(mutated), "-o", str(so)],
+                   check=True)
+    lib = ctypes.CDLL(str(so))
+    P, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.oracle_asral_q.argtypes = [i64, i64, P, P, P, i64, c_int, i64, c_int, P, P, P, P]
+    caught = False
+    for s in range(12):
+        J, q = _qinst(3700 + s, 24, 4, 6, cm_max=20, cap_frac=0.4)
+        cm = np.ascontiguousarray(J.cm, np.int32)
+        qq = np.ascontiguousarray(q, np.int32)
+        assign = np.empty(J.n, np.int32)
+        load = np.empty(J.k, np.int64)
+        delta = ctypes.c_int64(0)
+        st = oracle._Stats()
+        rc = lib.oracle_asral_q(J.n, J.k, cm.ctypes.data, J.cap.ctypes.data, qq.ctypes.data,
+                                q.shape[1], oracle.MODE_HEAP, -1, 1, assign.ctypes.data,
+                                load.ctypes.data, ctypes.byref(delta), ctypes.byref(st))
+        opt = exact.matching_optimum_q(J.cm, J.cap, q)
+        if rc != 0 or delta.value != opt or \
+                delta.value != exact.eq1_objective_q(J.cm, J.cap, q, assign):
+            caught = True
             break
     assert caught, f"mutation {name} escaped every pin"
