@@ -124,6 +124,18 @@ int lbdd_create(lbdd_solver** out, int32_t n, int32_t k, const void* cm, int cm_
 /* Set an lbdd_option; LBDD_ERR_ARG for an unknown option or bad value. */
 int lbdd_set_option(lbdd_solver* s, int option, int64_t value);
 
+/* General penalty functions (Def. 4): q_s(j), the extra cost of the j-th
+ * allotment beyond center s's capacity, positive and non-decreasing in j.
+ * qtab is a host k x Q table, q_s(j) = qtab[s*Q + min(j, Q) - 1] (the last
+ * value repeats); it replaces the constant pen[] given to lbdd_create (which
+ * is the Q = 1 table).  The allotment of Alg. 2 pays q_j(load - c + 1), the
+ * penalty edge of Def. 10 (c) costs q_u(load_u - c_u + 1) (0 with a vacancy)
+ * minus q_j(load_j - c_j), and the objective sums q_s(1..load - c).  Call
+ * before the first lbdd_solve (or after lbdd_reset).  Errors: LBDD_ERR_ARG
+ * (non-positive or decreasing rows, strict solver), LBDD_ERR_STATE (rounds
+ * already run). */
+int lbdd_set_penalty_table(lbdd_solver* s, const int32_t* qtab, int32_t Q);
+
 /* Create a solver for a strict-LBDD instance (Appendix B, Alg. 5, Theorem 2):
  * no center may exceed its capacity.  If the capacities sum to less than n,
  * a dummy center k is added with capacity n - sum(cap) and cost max(CM) + 1

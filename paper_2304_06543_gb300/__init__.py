@@ -19,7 +19,7 @@ import numpy as np
 from . import _build
 
 __all__ = [
-    "load", "LbddError", "Solver", "create", "create_strict", "solve", "reset", "solve_batch", "objective",
+    "load", "LbddError", "Solver", "create", "create_strict", "set_penalty_table", "solve", "reset", "solve_batch", "objective",
     "assignment", "loads", "rounds_done", "get_stats", "best_transfer_table",
     "best_transfer", "best_transfer_workspace", "cm_pitch", "strerror", "destroy",
     "Batch", "autotune", "tune_get", "tune_clear", "Server", "RequestInfo", "ServerStats",
@@ -87,6 +87,7 @@ def load():
         lib.lbdd_create.argtypes = [ctypes.POINTER(P), i32, i32, P, c_int, c_int, P, P, P]
         lib.lbdd_set_option.argtypes = [P, c_int, i64]
         lib.lbdd_create_strict.argtypes = [ctypes.POINTER(P), i32, i32, P, c_int, c_int, P, P]
+        lib.lbdd_set_penalty_table.argtypes = [P, P, i32]
         lib.lbdd_solve.argtypes = [P, i64]
         lib.lbdd_reset.argtypes = [P]
         lib.lbdd_solve_batch.argtypes = [ctypes.POINTER(P), c_int, i64, c_int, c_int, P]
@@ -223,6 +224,13 @@ def create_strict(n, k, cm, cap, stream=None):
     return h
 
 
+def set_penalty_table(h, qtab):
+    """lbdd_set_penalty_table: qtab (k, Q) int32, q_s(j) = qtab[s, min(j, Q) - 1]."""
+    q = np.ascontiguousarray(qtab, dtype=np.int32)
+    _check(load().lbdd_set_penalty_table(h, q.ctypes.data, int(q.shape[1])),
+           "lbdd_set_penalty_table")
+
+
 def set_option(h, option: int, value: int):
     _check(load().lbdd_set_option(h, option, value), "lbdd_set_option")
 
@@ -320,7 +328,8 @@ class Solver:
     penalties; the instance gains a dummy center when capacity is short)."""
 
     def __init__(self, cm, cap, pen, stream=None, cluster: int = 0, ncyc_skip: bool = True,
-                 npath_reuse: bool = True, phase_timers: bool = False, strict: bool = False):
+                 npath_reuse: bool = True, phase_timers: bool = False, strict: bool = False,
+                 qtab=None):
         if isinstance(cm, np.ndarray):
             n, k = cm.shape
         else:
@@ -340,6 +349,8 @@ class Solver:
             set_option(self.h, OPT_NPATH_REUSE, 0)
         if phase_timers:
             set_option(self.h, OPT_PHASE_TIMERS, 1)
+        if qtab is not None:
+            set_penalty_table(self.h, qtab)
 
     def solve(self, max_rounds: int = -1):
         solve(self.h, max_rounds)

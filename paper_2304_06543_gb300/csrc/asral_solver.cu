@@ -121,7 +121,7 @@ struct Solver {
   int32_t* s_hop;     // sweep of each owned column's last label change
   int32_t* s_load;
   int32_t* s_cap;     // capacity replica
-  int32_t* s_pen;     // penalty replica
+  int32_t* s_pen;     // [k] penalty one more unit would pay at each center, q_c(load_c - cap_c + 1)
   uint64_t* s_front;  // frontier keys ((label + 2^47) << 16 | node) of the current sweep
   int32_t* s_par;     // parents of the owned columns
   uint64_t* s_outbox; // [2][w + OB_SLOTS]: keys ((label + 2^47) << 16 | node) published per sweep
@@ -519,6 +519,15 @@ struct Solver {
     return best;
   }
 
+  // q_c(x), x >= 1: penalty of the x-th allotment beyond capacity (Def. 4).
+  __device__ __forceinline__ int32_t qval(int32_t c, int32_t x) const {
+    return __ldg(I.pen + (int64_t)c * I.Q + min(max(x, 1), I.Q) - 1);
+  }
+  // Penalty replica entry of center c for its current load.
+  __device__ __forceinline__ int32_t qnext(int32_t c) const {
+    return qval(c, s_load[c] - s_cap[c] + 1);
+  }
+
   // Alg. 5 edge cost: a center with a vacancy can pass a dummy unit on for
   // free, so its transfer costs are min(T, 0) (an absent edge becomes 0).
   __device__ __forceinline__ int32_t strict_cost(int32_t t, int32_t u, int32_t inf) const {
@@ -580,7 +589,8 @@ struct Solver {
     }
     __syncthreads();
     const int owner_j = j / w;
-    const int32_t pen_j = __ldg(I.pen + j);
+    // NPath (Def. 10 (c)): the penalty the anchor's last unit beyond capacity paid
+    const int32_t pen_j = npath ? qval(j, s_load[j] - s_cap[j]) : 0;
     const int obs = w + (int)kOutboxExtra;
     const bool strict = flags & OPT_STRICT;
     // lanes own 32 consecutive columns (a column block); the WPB warps of a
@@ -728,7 +738,7 @@ struct Solver {
   // exchanged, and every CTA combines the same partials.  Returns 1 if the
   // sink label is negative.
   __device__ int npath_from_ncyc(int32_t j) {
-    const int32_t pen_j = __ldg(I.pen + j);
+    const int32_t pen_j = qval(j, s_load[j] - s_cap[j]);
     int64_t bc = kDInf;
     uint32_t bhu = 0xffffffffu;   // hop << 16 | node
     auto better = [](int64_t c, uint32_t hu, int64_t bc_, uint32_t bhu_) {
@@ -868,9 +878,11 @@ struct Solver {
         B->delta += s_misc[MS_SINK_DIST];
       }
     }
-    if (npath && tid == 0) {   // load replicas in every CTA
+    if (npath && tid == 0) {   // load and penalty replicas in every CTA
       s_load[j] -= 1;
       s_load[s_path[m - 1]] += 1;
+      s_pen[j] = qnext(j);
+      s_pen[s_path[m - 1]] = qnext(s_path[m - 1]);
     }
     if ((flags & OPT_STRICT) && tid == 0) {
       for (int i = 0; i < m; ++i) {
@@ -973,7 +985,7 @@ struct Solver {
     for (int v = tid; v < k; v += kThreads) {
       s_load[v] = __ldcg(I.load + v);
       s_cap[v] = __ldg(I.cap + v);
-      s_pen[v] = __ldg(I.pen + v);
+      s_pen[v] = qval(v, s_load[v] - s_cap[v] + 1);
     }
     if (rank == 0 && tid == 0) {
       B->delta = I.ctl[CTL_DELTA];
@@ -1013,13 +1025,17 @@ struct Solver {
       const int32_t j = strict ? strict_target(d) : __ldcg(I.smin + d);
       if ((uint32_t)j >= (uint32_t)k) { status = ST_ERR_INVARIANT; break; }
       const bool over = !strict && s_load[j] >= __ldg(I.cap + j);
+      const int32_t q_over = over ? s_pen[j] : 0;   // q_j(load - cap + 1), Alg. 2
       const bool merged = merge_row(d, j);
-      if (tid == 0) s_load[j] += 1;
+      if (tid == 0) {
+        s_load[j] += 1;
+        if (!strict) s_pen[j] = qnext(j);
+      }
       if (rank == 0 && tid == 0) {
         // Member lists are touched only after the next cluster barrier (the
         // first Bellman-Ford sweep), when every CTA has finished reading
         // them for the previous round's rescans.
-        B->delta += (int64_t)row(d)[j] + (over ? (int64_t)__ldg(I.pen + j) : 0);
+        B->delta += (int64_t)row(d)[j] + q_over;
         if (timer()) B->t_merge += clock_cycles() - tm0;
       }
       __syncthreads();

@@ -250,7 +250,7 @@ static int create_impl(lbdd_solver** out, int32_t n, int32_t k, const void* cm, 
   if (!rc) rc = dalloc(s, &s->d_inst, 1);
   if (rc) { free_all(s); delete s; return rc; }
   DevInst& I = s->h_inst;
-  I.cm = s->cm; I.ld = s->ld; I.n = n; I.k = k; I.cap = s->cap; I.pen = s->pen;
+  I.cm = s->cm; I.ld = s->ld; I.n = n; I.k = k; I.cap = s->cap; I.pen = s->pen; I.Q = 1;
   I.smin = s->smin; I.order = s->order; I.sort_tmp = s->sort_tmp; I.assign = s->assign;
   I.pos = s->pos; I.load = s->load; I.seg_size = s->seg_size; I.page_tab = s->page_tab;
   I.pool = s->pool; I.free_stack = s->free_stack; I.tc = s->tc; I.td = s->td; I.ctl = s->ctl;
@@ -354,12 +354,41 @@ extern "C" int lbdd_create_strict(lbdd_solver** out, int32_t n, int32_t k, const
 }
 
 int lbdd::clone_solver(const lbdd_solver* src, lbdd_solver** out) {
-  std::vector<int32_t> cap(src->k), pen(src->k);
+  const int32_t Q = src->h_inst.Q;
+  std::vector<int32_t> cap(src->k), q((size_t)src->k * Q), pen(src->k);
   CK(cudaMemcpyAsync(cap.data(), src->cap, 4ull * src->k, cudaMemcpyDeviceToHost, src->st));
-  CK(cudaMemcpyAsync(pen.data(), src->pen, 4ull * src->k, cudaMemcpyDeviceToHost, src->st));
+  CK(cudaMemcpyAsync(q.data(), src->h_inst.pen, 4ull * src->k * Q, cudaMemcpyDeviceToHost,
+                     src->st));
   CK(cudaStreamSynchronize(src->st));
-  return create_impl(out, src->n, src->k, src->cm, src->elem == 2 ? LBDD_CM_I16 : LBDD_CM_I32, 1,
-                     src->ld, cap.data(), pen.data(), src->st);
+  for (int32_t c = 0; c < src->k; ++c) pen[c] = q[(size_t)c * Q];
+  int rc = create_impl(out, src->n, src->k, src->cm, src->elem == 2 ? LBDD_CM_I16 : LBDD_CM_I32,
+                       1, src->ld, cap.data(), pen.data(), src->st);
+  if (rc == LBDD_OK && Q > 1) rc = lbdd_set_penalty_table(*out, q.data(), Q);
+  if (rc == LBDD_OK) { (*out)->strict = src->strict; }
+  return rc;
+}
+
+extern "C" int lbdd_set_penalty_table(lbdd_solver* s, const int32_t* qtab, int32_t Q) {
+  if (!s || !qtab || Q < 1 || s->strict) return LBDD_ERR_ARG;
+  for (int32_t c = 0; c < s->k; ++c)
+    for (int32_t j = 0; j < Q; ++j) {
+      const int32_t v = qtab[(size_t)c * Q + j];
+      if (v < 1 || (j > 0 && v < qtab[(size_t)c * Q + j - 1])) return LBDD_ERR_ARG;
+    }
+  int64_t rounds = 0;
+  CK(cudaMemcpyAsync(&rounds, s->ctl + CTL_PROLOGUE, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                     s->st));
+  CK(cudaStreamSynchronize(s->st));
+  if (rounds != 0) return LBDD_ERR_STATE;   // only before the first round (or after a reset)
+  int32_t* table = nullptr;
+  int rc = dalloc(s, &table, (size_t)s->k * Q);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(table, qtab, 4ull * s->k * Q, cudaMemcpyHostToDevice, s->st));
+  s->h_inst.pen = table;
+  s->h_inst.Q = Q;
+  CK(cudaMemcpyAsync(s->d_inst, &s->h_inst, sizeof(DevInst), cudaMemcpyHostToDevice, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return LBDD_OK;
 }
 
 extern "C" int lbdd_set_option(lbdd_solver* s, int option, int64_t value) {

@@ -77,7 +77,8 @@ struct DevInst {
   int64_t ld;           // row pitch in elements (multiple of 16 bytes)
   int32_t n, k;
   const int32_t* cap;   // k
-  const int32_t* pen;   // k
+  const int32_t* pen;   // k x Q penalty table: q_s(j) = pen[s*Q + min(j, Q) - 1] (Def. 4)
+  int32_t Q;            // table length (1: constant per-unit penalty)
   int32_t* smin;        // n: most suitable center
   int32_t* order;       // n: MinDistance extraction order
   int32_t* sort_tmp;    // 3n: radix-sort scratch
