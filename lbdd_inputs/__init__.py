@@ -225,6 +225,71 @@ def make_named(name: str, dtype: str = "i32", **overrides) -> Instance:
     return make(r, dtype=dtype)
 
 
+@dataclass
+class RoadNetwork:
+    """Directed CSR graph (both directions of every road), node coordinates,
+    and the centers / demand nodes chosen on it."""
+    V: int
+    row_ptr: np.ndarray      # (V + 1,) int32
+    col: np.ndarray          # (E,) int32
+    w: np.ndarray            # (E,) int32, >= 1
+    xy: np.ndarray           # (V, 2) float64
+    centers: np.ndarray      # (k,) int32 node ids
+    demand: np.ndarray       # (n,) int32 node ids (every other node)
+
+
+def road_network(seed: int, W: int, H: int, k: int, diag_frac: float = 0.15) -> RoadNetwork:
+    """Synthetic road network standing in for the paper's New Delhi graph
+    (Section 5): a W x H grid of intersections (jittered positions) with
+    4-neighbour roads plus a fraction of diagonal roads; road length =
+    floor(100 * euclidean * rf + 0.5) with rf in [1, 1.5] per road, at least
+    1.  k distinct nodes become service centers, every other node is one
+    unit of demand.  All draws come from the counter stream of `seed`."""
+    lib = _load()
+    V = W * H
+    u01 = lambda st, i: lib.lbdd_gen_u01(seed, st, i)
+    xy = np.empty((V, 2), np.float64)
+    for v in range(V):
+        x, y = v % W, v // W
+        xy[v, 0] = (x + 0.35 * (u01(70, 2 * v) - 0.5)) / W
+        xy[v, 1] = (y + 0.35 * (u01(70, 2 * v + 1) - 0.5)) / H
+    roads = []
+    for v in range(V):
+        x, y = v % W, v // W
+        if x + 1 < W:
+            roads.append((v, v + 1))
+        if y + 1 < H:
+            roads.append((v, v + W))
+        if x + 1 < W and y + 1 < H and u01(71, v) < diag_frac:
+            roads.append((v, v + W + 1))
+    adj = [[] for _ in range(V)]
+    for i, (a, b) in enumerate(roads):
+        dx, dy = xy[a] - xy[b]
+        rf = 1.0 + 0.5 * u01(72, i)
+        wt = max(1, int(np.floor(100.0 * np.sqrt(dx * dx + dy * dy) * W * rf + 0.5)))
+        adj[a].append((b, wt))
+        adj[b].append((a, wt))
+    row_ptr = np.zeros(V + 1, np.int32)
+    for v in range(V):
+        row_ptr[v + 1] = row_ptr[v] + len(adj[v])
+    col = np.empty(row_ptr[-1], np.int32)
+    w = np.empty(row_ptr[-1], np.int32)
+    for v in range(V):
+        for i, (b, wt) in enumerate(sorted(adj[v])):
+            col[row_ptr[v] + i] = b
+            w[row_ptr[v] + i] = wt
+    # k distinct centers by a seeded partial shuffle
+    perm = np.arange(V, dtype=np.int64)
+    for i in range(k):
+        j = i + int(lib.lbdd_gen_u64(seed, 73, i) % (V - i))
+        perm[i], perm[j] = perm[j], perm[i]
+    centers = np.sort(perm[:k]).astype(np.int32)
+    is_c = np.zeros(V, bool)
+    is_c[centers] = True
+    demand = np.nonzero(~is_c)[0].astype(np.int32)
+    return RoadNetwork(V=V, row_ptr=row_ptr, col=col, w=w, xy=xy, centers=centers, demand=demand)
+
+
 def penalty_table(seed: int, k: int, Q: int, base=(1, 30), step=(0, 10)) -> np.ndarray:
     """General penalty functions (Def. 4) as a k x Q table: q_s(j) for the
     j-th allotment beyond capacity, j = 1..Q (the last value repeats).

@@ -55,6 +55,7 @@ def _load():
         lib.oracle_has_negative_cycle.argtypes = [i64, P]
         lib.oracle_asral.argtypes = [i64, i64, P, P, P, c_int, i64, c_int, P, P, P, P]
         lib.oracle_asral_q.argtypes = [i64, i64, P, P, P, i64, c_int, i64, c_int, P, P, P, P]
+        lib.oracle_road_cm.argtypes = [i64, P, P, P, i64, P, i64, P, P]
         lib.oracle_objective_q.argtypes = [i64, i64, P, P, P, i64, P]
         lib.oracle_objective_q.restype = i64
         lib.oracle_strict.argtypes = [i64, i64, P, P, P, P, P]
@@ -169,6 +170,17 @@ def asral_q(cm, cap, qtab, mode=MODE_HEAP, max_rounds=-1, check=False) -> Result
                                 ctypes.byref(delta), ctypes.byref(st))
     stats = {f: getattr(st, f) for f, _ in _Stats._fields_}
     return Result(assign=assign, load=load, delta=int(delta.value), stats=stats, rc=rc)
+
+
+def road_cm(row_ptr, col, w, centers, demand):
+    """CM from shortest paths on a road network (Section 3.4): (rc, CM n x k)."""
+    row_ptr, col, w = _c(row_ptr, np.int32), _c(col, np.int32), _c(w, np.int32)
+    centers, demand = _c(centers, np.int32), _c(demand, np.int32)
+    V, k, n = len(row_ptr) - 1, len(centers), len(demand)
+    cm = np.zeros((n, k), np.int32)
+    rc = _load().oracle_road_cm(V, _p(row_ptr), _p(col), _p(w), k, _p(centers), n, _p(demand),
+                                _p(cm))
+    return rc, cm
 
 
 def strict(cm, cap):

@@ -698,3 +698,82 @@ int oracle_strict(int64_t n, int64_t k, const int32_t *cm, const int32_t *cap, i
     free(mv_u); free(mv_from); free(mv_to);
     return rc;
 }
+
+/* ------------------------------------------------------------------------
+ * Cost matrix from a road network (Section 3.4 "Demand-service cost matrix
+ * construction", Section 5 "Datasets"): CM(d, s) is the shortest-path length
+ * from center node centers[s] to demand node demand[d] over the directed
+ * graph (row_ptr, col, w) with positive integer lengths.  Plain Dijkstra
+ * with a binary heap, one source at a time.  Returns OR_ERR_ARG for a bad
+ * graph or an unreachable demand node.
+ */
+typedef struct { int64_t key; int32_t v; } dj_item;
+
+static void dj_push(dj_item *h, int64_t *len, int64_t key, int32_t v) {
+    int64_t i = (*len)++;
+    h[i].key = key; h[i].v = v;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (h[p].key <= h[i].key) break;
+        dj_item t = h[p]; h[p] = h[i]; h[i] = t;
+        i = p;
+    }
+}
+
+static dj_item dj_pop(dj_item *h, int64_t *len) {
+    dj_item top = h[0];
+    h[0] = h[--(*len)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, m = i;
+        if (l < *len && h[l].key < h[m].key) m = l;
+        if (r < *len && h[r].key < h[m].key) m = r;
+        if (m == i) break;
+        dj_item t = h[m]; h[m] = h[i]; h[i] = t;
+        i = m;
+    }
+    return top;
+}
+
+int oracle_road_cm(int64_t V, const int32_t *row_ptr, const int32_t *col, const int32_t *w,
+                   int64_t k, const int32_t *centers, int64_t n, const int32_t *demand,
+                   int32_t *cm_out) {
+    if (V < 1 || k < 1 || n < 1 || !row_ptr || !col || !w || !centers || !demand || !cm_out)
+        return OR_ERR_ARG;
+    int64_t E = row_ptr[V];
+    for (int64_t e = 0; e < E; ++e)
+        if (w[e] < 1 || col[e] < 0 || col[e] >= V) return OR_ERR_ARG;
+    int64_t *dist = (int64_t *)malloc(sizeof(int64_t) * (size_t)V);
+    dj_item *heap = (dj_item *)malloc(sizeof(dj_item) * (size_t)(E + 1));
+    if (!dist || !heap) { free(dist); free(heap); return OR_ERR_OOM; }
+    int rc = OR_OK;
+    for (int64_t s = 0; s < k && rc == OR_OK; ++s) {
+        if (centers[s] < 0 || centers[s] >= V) { rc = OR_ERR_ARG; break; }
+        for (int64_t v = 0; v < V; ++v) dist[v] = OR_INF;
+        int64_t len = 0;
+        dist[centers[s]] = 0;
+        dj_push(heap, &len, 0, centers[s]);
+        while (len > 0) {
+            dj_item it = dj_pop(heap, &len);
+            if (it.key > dist[it.v]) continue;   /* stale entry */
+            for (int32_t e = row_ptr[it.v]; e < row_ptr[it.v + 1]; ++e) {
+                int64_t nd = it.key + w[e];
+                if (nd < dist[col[e]]) {
+                    dist[col[e]] = nd;
+                    dj_push(heap, &len, nd, col[e]);
+                }
+            }
+        }
+        for (int64_t d = 0; d < n; ++d) {
+            int32_t v = demand[d];
+            if (v < 0 || v >= V || dist[v] >= OR_INF || dist[v] < 1 || dist[v] > INT32_MAX) {
+                rc = OR_ERR_ARG;
+                break;
+            }
+            cm_out[d * k + s] = (int32_t)dist[v];
+        }
+    }
+    free(dist);
+    free(heap);
+    return rc;
+}

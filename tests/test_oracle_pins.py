@@ -366,3 +366,53 @@ def test_planted_penalty_table_mistake_is_caught(name, tmp_path):
             caught = True
             break
     assert caught, f"mutation {name} escaped every pin"
+
+
+# ------------------------------------------------ road-network cost matrix --
+
+def _grid_csr(W, H, weight=1):
+    adj = [[] for _ in range(W * H)]
+    for v in range(W * H):
+        x, y = v % W, v // W
+        for dx, dy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+            if 0 <= x + dx < W and 0 <= y + dy < H:
+                adj[v].append(v + dx + dy * W)
+    row_ptr = np.zeros(W * H + 1, np.int32)
+    for v in range(W * H):
+        row_ptr[v + 1] = row_ptr[v] + len(adj[v])
+    col = np.array([b for a in adj for b in sorted(a)], np.int32)
+    return row_ptr, col, np.full(len(col), weight, np.int32)
+
+
+def test_road_cm_unit_grid_is_manhattan():
+    """On a unit-length grid the shortest path is the Manhattan distance."""
+    W, H = 13, 9
+    row_ptr, col, w = _grid_csr(W, H, weight=3)
+    centers = np.array([0, 17, 60, 116], np.int32)
+    demand = np.array([v for v in range(W * H) if v not in set(centers)], np.int32)
+    rc, cm = oracle.road_cm(row_ptr, col, w, centers, demand)
+    assert rc == 0
+    for d, v in enumerate(demand):
+        for s, c in enumerate(centers):
+            assert cm[d, s] == 3 * (abs(v % W - c % W) + abs(v // W - c // W))
+
+
+def test_road_cm_equals_scipy_dijkstra():
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import dijkstra
+    g = L.road_network(11, 24, 17, 6)
+    rc, cm = oracle.road_cm(g.row_ptr, g.col, g.w, g.centers, g.demand)
+    assert rc == 0
+    A = csr_matrix((g.w.astype(np.float64), g.col, g.row_ptr), shape=(g.V, g.V))
+    D = dijkstra(A, directed=True, indices=g.centers)
+    assert np.array_equal(cm, D[:, g.demand].T.astype(np.int64))
+
+
+def test_road_cm_rejects_bad_graph():
+    row_ptr, col, w = _grid_csr(4, 4)
+    w[3] = 0
+    assert oracle.road_cm(row_ptr, col, w, [0], [5])[0] == oracle.ERR_ARG
+    # an isolated demand node is unreachable
+    row_ptr2 = np.append(row_ptr, row_ptr[-1]).astype(np.int32)
+    _, col2, w2 = _grid_csr(4, 4)
+    assert oracle.road_cm(row_ptr2, col2, w2, [0], [16])[0] == oracle.ERR_ARG
