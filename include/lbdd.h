@@ -349,6 +349,25 @@ int lbdd_best_transfer_noalloc(int32_t n, int32_t k, const void* cm_dev, int cm_
                                const int32_t* assign_dev, int32_t* tc_dev, int32_t* td_dev,
                                void* stream);
 
+/* ---------------------------------------------------------------------
+ * Cost matrix from a road network (Section 3.4 "Demand-service cost matrix
+ * construction": shortest paths when centers and demand lie on a road
+ * network; Section 5 uses the New Delhi network this way).
+ *   V            : nodes; row_ptr (V + 1), col, w (row_ptr[V] each): a
+ *                  directed CSR graph, lengths w >= 1 (give both directions
+ *                  of a two-way road); (V - 1) * max(w) must be < 2^31.
+ *   centers (k)  : center nodes; demand (n): one node per demand unit.
+ *   cm (n x ld)  : output, int32, CM[d * ld + s] = shortest path length from
+ *                  centers[s] to demand[d] (ld >= k).
+ * All arrays are device memory; work is ordered on `stream` and the call
+ * waits for it.  Scratch (k x V labels and per-CTA frontier queues) is
+ * allocated from the stream-ordered pool and freed before returning.
+ * Errors: LBDD_ERR_ARG (bad graph or ids, lengths that could overflow, a
+ * demand node no center reaches), LBDD_ERR_CUDA, LBDD_ERR_OOM. */
+int lbdd_road_cm(int32_t V, const int32_t* row_ptr, const int32_t* col, const int32_t* w,
+                 int32_t k, const int32_t* centers, int32_t n, const int32_t* demand,
+                 int32_t* cm, int64_t ld, void* stream);
+
 /* Row pitch (elements) that lbdd_create uses for a CM of k columns, and the
  * device pointer / pitch of a solver's stored CM (for lbdd_best_transfer). */
 int64_t lbdd_cm_pitch(int32_t k, int cm_dtype);

@@ -19,7 +19,7 @@ import numpy as np
 from . import _build
 
 __all__ = [
-    "load", "LbddError", "Solver", "create", "create_strict", "set_penalty_table", "solve", "reset", "solve_batch", "objective",
+    "load", "LbddError", "Solver", "create", "create_strict", "set_penalty_table", "road_cm", "solve", "reset", "solve_batch", "objective",
     "assignment", "loads", "rounds_done", "get_stats", "best_transfer_table",
     "best_transfer", "best_transfer_workspace", "cm_pitch", "strerror", "destroy",
     "Batch", "autotune", "tune_get", "tune_clear", "Server", "RequestInfo", "ServerStats",
@@ -88,6 +88,7 @@ def load():
         lib.lbdd_set_option.argtypes = [P, c_int, i64]
         lib.lbdd_create_strict.argtypes = [ctypes.POINTER(P), i32, i32, P, c_int, c_int, P, P]
         lib.lbdd_set_penalty_table.argtypes = [P, P, i32]
+        lib.lbdd_road_cm.argtypes = [i32, P, P, P, i32, P, i32, P, P, i64, P]
         lib.lbdd_solve.argtypes = [P, i64]
         lib.lbdd_reset.argtypes = [P]
         lib.lbdd_solve_batch.argtypes = [ctypes.POINTER(P), c_int, i64, c_int, c_int, P]
@@ -222,6 +223,16 @@ def create_strict(n, k, cm, cap, stream=None):
     _check(lib.lbdd_create_strict(ctypes.byref(h), int(n), int(k), cm.ctypes.data, dt, 0,
                                   cap.ctypes.data, _stream_handle(stream)), "lbdd_create_strict")
     return h
+
+
+def road_cm(row_ptr, col, w, centers, demand, out, ld=None, stream=None):
+    """lbdd_road_cm on device tensors (int32); out: device int32 (n, ld)."""
+    n, k = len(demand), len(centers)
+    _check(load().lbdd_road_cm(int(len(row_ptr) - 1), _dptr(row_ptr), _dptr(col), _dptr(w),
+                               int(k), _dptr(centers), int(n), _dptr(demand), _dptr(out),
+                               int(ld if ld is not None else k), _stream_handle(stream)),
+           "lbdd_road_cm")
+    return out
 
 
 def set_penalty_table(h, qtab):

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbdd.so")
 
 SOURCES = ["asral_solver.cu", "best_transfer.cu", "lbdd_api.cu", "best_transfer_noalloc.cu",
-           "lbdd_batch.cu", "lbdd_server.cu"]
+           "lbdd_batch.cu", "lbdd_server.cu", "road_cm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
