@@ -38,6 +38,7 @@ struct BtWorkspace {
   int4* items;                  // explicit work items {center, first row, rows, 0}
   int* err;                     // [0] unused, [1] the work-item queue counter
   int32_t* dsum;                // 256 digit totals of a radix pass
+  int32_t* ownv;                // n: CM(d, center of d) in sorted order (int16 scan)
   int64_t ntiles;
   size_t bytes;
 };
@@ -65,6 +66,7 @@ static BtWorkspace carve(void* base, int32_t n, int32_t k) {
   W.items = reinterpret_cast<int4*>(take(16ull * ((size_t)n / kChunk + (size_t)k + 1)));
   W.err = reinterpret_cast<int*>(take(16));   // err, then the item queue counter
   W.dsum = reinterpret_cast<int32_t*>(take(4 * 256));
+  W.ownv = reinterpret_cast<int32_t*>(take(4ull * n));
   W.bytes = o;
   return W;
 }
@@ -237,16 +239,21 @@ __global__ void __launch_bounds__(kThreads) bt_scatter(const int32_t* __restrict
   }
 }
 
-// Segment bounds of the sorted keys.
+// Segment bounds of the sorted keys; with cm16, also the own cost
+// CM(d, c) of every sorted unit (for the staged int16 scan).
 __global__ void __launch_bounds__(kThreads) bt_bounds(const int32_t* __restrict__ keys,
+                                                      const int32_t* __restrict__ vals,
                                                       int32_t n, int32_t k, int32_t* seg_start,
-                                                      int32_t* seg_end) {
+                                                      int32_t* seg_end,
+                                                      const int16_t* __restrict__ cm16, int64_t ld,
+                                                      int32_t* ownv) {
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kThreads) {
     const int32_t c = keys[i];
     if (c >= k) continue;
     if (i == 0 || keys[i - 1] != c) seg_start[c] = (int32_t)i;
     if (i == n - 1 || keys[i + 1] != c) seg_end[c] = (int32_t)i + 1;
+    if (cm16) ownv[i] = cm16[(int64_t)vals[i] * ld + c];
   }
 }
 
@@ -397,6 +404,127 @@ bt_scan_rows(const T* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
   }
 }
 
+// ------------------------------------------------ staged int16 row scan ---
+//
+// The int16 scan of the rows of an item, with each thread's 16-byte chunk of
+// a row copied global -> shared by cp.async kStages rows ahead: the bytes in
+// flight are bounded by shared memory, not by registers.  A thread waits only
+// for its own copies (cp.async.wait_group), so no barrier is involved.  Unit
+// ids and own costs (CM(d, c), gathered in sorted order by bt_bounds) travel
+// in register rings two and one stages ahead.  Keys as in bt_scan_rows.
+constexpr int kStages = 10;
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+size_t bt_staged_smem_bytes() {
+  return (size_t)kStages * kThreads * 16 + (size_t)kThreads * 8 * sizeof(int2);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+bt_scan_rows_staged16(const int16_t* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
+                      const int32_t* __restrict__ perm, const int32_t* __restrict__ ownv,
+                      const int32_t* __restrict__ item_off, const int4* __restrict__ items,
+                      unsigned long long* t64, int* work) {
+  constexpr int VPL = 8, P = kStages;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  uint4* stage = reinterpret_cast<uint4*>(dsm);                           // [P][kThreads]
+  int2* red = reinterpret_cast<int2*>(dsm + (size_t)P * kThreads * 16);  // [kThreads * VPL]
+  __shared__ int s_item[2];
+  const int S = (k + VPL - 1) / VPL;
+  const int R = kThreads / S;
+  const int tid = threadIdx.x, slot = tid % S, g = tid / S;
+  const int32_t total = item_off[k];
+  if (tid == 0) s_item[0] = atomicAdd(work, 1);
+  __syncthreads();
+  for (int32_t item = s_item[0];;) {
+    if (item >= total) break;
+    const int4 desc = items[item];
+    if (tid == 0) s_item[1] = atomicAdd(work, 1);
+    const int32_t c = desc.x, r0 = desc.y, cnt = desc.z;
+    uint32_t key[VPL];
+#pragma unroll
+    for (int q = 0; q < VPL; ++q) key[q] = 0xffffffffu;
+    if (g < R && g < cnt) {
+      const int32_t M = (cnt - g + R - 1) / R;        // rows of this thread: g + m * R
+      auto row_id = [&](int32_t m) -> int32_t {
+        return m < M ? (int32_t)min((uint32_t)__ldg(perm + r0 + g + m * R), (uint32_t)(n - 1)) : 0;
+      };
+      auto row_own = [&](int32_t m) -> int32_t { return m < M ? __ldg(ownv + r0 + g + m * R) : 0; };
+      int32_t idA[P], ownA[P], idB[P], ownB[P], ownS[P];
+      // rows 0..P-1 go to the stages now, rows P..2P-1 and 2P..3P-1 are prefetched
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const int32_t d0 = row_id(q);
+        ownS[q] = row_own(q);
+        if (q < M) cp_async16(&stage[q * kThreads + tid], cm + (int64_t)d0 * ld + slot * VPL);
+        cp_async_commit();
+        idA[q] = row_id(P + q);
+        ownA[q] = row_own(P + q);
+        idB[q] = row_id(2 * P + q);
+        ownB[q] = row_own(2 * P + q);
+      }
+      for (int32_t m = 0; m < M; m += P) {
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          cp_async_wait<P - 1>();                     // row m + q has landed
+          if (m + q < M) {
+            const uint4 wv = stage[q * kThreads + tid];
+            const uint32_t crow = ((uint32_t)(32768 - ownS[q]) << 16) | (uint32_t)(g + (m + q) * R);
+            const uint32_t w4[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              key[2 * h] = min(key[2 * h], (w4[h] << 16) + crow);
+              key[2 * h + 1] = min(key[2 * h + 1], (w4[h] & 0xffff0000u) + crow);
+            }
+          }
+          // stage q now takes row m + q + P
+          if (m + q + P < M) cp_async16(&stage[q * kThreads + tid], cm + (int64_t)idA[q] * ld + slot * VPL);
+          cp_async_commit();
+          ownS[q] = ownA[q];
+          idA[q] = idB[q];
+          ownA[q] = ownB[q];
+          idB[q] = row_id(m + q + 3 * P);
+          ownB[q] = row_own(m + q + 3 * P);
+        }
+      }
+      cp_async_wait<0>();
+    }
+    if (g < R) {
+#pragma unroll
+      for (int q = 0; q < VPL; ++q) {
+        int32_t bt = kTInf, bd = -1;
+        if (key[q] != 0xffffffffu) {
+          bt = (int32_t)(key[q] >> 16) - 32768;
+          bd = (int32_t)min((uint32_t)__ldg(perm + r0 + (int32_t)(key[q] & 0xffffu)), (uint32_t)(n - 1));
+        }
+        red[g * S * VPL + slot * VPL + q] = make_int2(bt, bd);
+      }
+    }
+    __syncthreads();
+    for (int col = tid; col < k; col += kThreads) {
+      int32_t t = kTInf, dd = -1;
+      for (int gg = 0; gg < R; ++gg) {
+        const int2 e = red[gg * S * VPL + col];
+        if (lex_less(e.x, e.y, t, dd)) { t = e.x; dd = e.y; }
+      }
+      if (dd >= 0 && col != c) {
+        const unsigned long long kk =
+            ((unsigned long long)(uint32_t)(t + (int64_t)2147483648LL) << 32) | (uint32_t)dd;
+        atomicMin(&t64[(int64_t)c * k + col], kk);
+      }
+    }
+    item = s_item[1];
+    __syncthreads();
+    if (tid == 0) s_item[0] = item;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) bt_unpack(const unsigned long long* __restrict__ t64,
                                                       int32_t k, int32_t* tc, int32_t* td,
                                                       const int* err) {
@@ -442,15 +570,27 @@ cudaError_t best_transfer_run(int32_t n, int32_t k, const void* cm, int elem_byt
   }
   cudaMemsetAsync(W.seg_start, 0, 4ull * k, st);
   cudaMemsetAsync(W.seg_end, 0, 4ull * k, st);
-  bt_bounds<<<grid_lin, kThreads, 0, st>>>(sk, n, k, W.seg_start, W.seg_end);
+  bt_bounds<<<grid_lin, kThreads, 0, st>>>(sk, sv, n, k, W.seg_start, W.seg_end,
+                                            elem_bytes == 2 ? static_cast<const int16_t*>(cm)
+                                                            : nullptr,
+                                            ld, W.ownv);
   bt_items<<<grid_lin, kThreads, 0, st>>>(W.seg_start, W.seg_end, k, W.item_off, W.t64);
   bt_scan<<<1, kThreads, 0, st>>>(W.item_off, k, W.item_off + k);
   const int grid_scan = num_sms;
   cudaMemsetAsync(W.err, 0, 2 * sizeof(int), st);
   bt_item_list<<<grid_lin, kThreads, 0, st>>>(W.seg_start, W.seg_end, W.item_off, k, W.items);
   if (elem_bytes == 2) {
-    bt_scan_rows<int16_t><<<grid_scan, kThreads, 0, st>>>(
-        static_cast<const int16_t*>(cm), ld, n, k, sv, W.item_off, W.items, W.t64, W.err + 1);
+    static bool attr_set = false;   // the staged kernel's dynamic shared memory
+    if (!attr_set) {
+      const cudaError_t e = cudaFuncSetAttribute(
+          bt_scan_rows_staged16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+          (int)bt_staged_smem_bytes());
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+    bt_scan_rows_staged16<<<grid_scan, kThreads, bt_staged_smem_bytes(), st>>>(
+        static_cast<const int16_t*>(cm), ld, n, k, sv, W.ownv, W.item_off, W.items, W.t64,
+        W.err + 1);
   } else {
     bt_scan_rows<int32_t><<<grid_scan, kThreads, 0, st>>>(
         static_cast<const int32_t*>(cm), ld, n, k, sv, W.item_off, W.items, W.t64, W.err + 1);
