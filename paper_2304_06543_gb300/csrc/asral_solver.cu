@@ -523,9 +523,15 @@ struct Solver {
   __device__ __forceinline__ int32_t qval(int32_t c, int32_t x) const {
     return __ldg(I.pen + (int64_t)c * I.Q + min(max(x, 1), I.Q) - 1);
   }
-  // Penalty replica entry of center c for its current load.
+  // Penalty replica entry of center c for its current load.  With a
+  // constant penalty (Q = 1) the replica never changes, so callers skip the
+  // update (a global load on the round's critical path).
   __device__ __forceinline__ int32_t qnext(int32_t c) const {
     return qval(c, s_load[c] - s_cap[c] + 1);
+  }
+  // q_j of the anchor's last unit beyond capacity (load > cap).
+  __device__ __forceinline__ int32_t qlast(int32_t j) const {
+    return I.Q == 1 ? s_pen[j] : qval(j, s_load[j] - s_cap[j]);
   }
 
   // Alg. 5 edge cost: a center with a vacancy can pass a dummy unit on for
@@ -590,7 +596,7 @@ struct Solver {
     __syncthreads();
     const int owner_j = j / w;
     // NPath (Def. 10 (c)): the penalty the anchor's last unit beyond capacity paid
-    const int32_t pen_j = npath ? qval(j, s_load[j] - s_cap[j]) : 0;
+    const int32_t pen_j = npath ? qlast(j) : 0;
     const int obs = w + (int)kOutboxExtra;
     const bool strict = flags & OPT_STRICT;
     // lanes own 32 consecutive columns (a column block); the WPB warps of a
@@ -738,7 +744,7 @@ struct Solver {
   // exchanged, and every CTA combines the same partials.  Returns 1 if the
   // sink label is negative.
   __device__ int npath_from_ncyc(int32_t j) {
-    const int32_t pen_j = qval(j, s_load[j] - s_cap[j]);
+    const int32_t pen_j = qlast(j);
     int64_t bc = kDInf;
     uint32_t bhu = 0xffffffffu;   // hop << 16 | node
     auto better = [](int64_t c, uint32_t hu, int64_t bc_, uint32_t bhu_) {
@@ -881,8 +887,10 @@ struct Solver {
     if (npath && tid == 0) {   // load and penalty replicas in every CTA
       s_load[j] -= 1;
       s_load[s_path[m - 1]] += 1;
-      s_pen[j] = qnext(j);
-      s_pen[s_path[m - 1]] = qnext(s_path[m - 1]);
+      if (I.Q > 1) {
+        s_pen[j] = qnext(j);
+        s_pen[s_path[m - 1]] = qnext(s_path[m - 1]);
+      }
     }
     if ((flags & OPT_STRICT) && tid == 0) {
       for (int i = 0; i < m; ++i) {
@@ -1029,7 +1037,7 @@ struct Solver {
       const bool merged = merge_row(d, j);
       if (tid == 0) {
         s_load[j] += 1;
-        if (!strict) s_pen[j] = qnext(j);
+        if (!strict && I.Q > 1) s_pen[j] = qnext(j);
       }
       if (rank == 0 && tid == 0) {
         // Member lists are touched only after the next cluster barrier (the
