@@ -355,9 +355,12 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int16",
             "data": "synthetic (seeded generator; the paper's New Delhi road network is not "
                     "available)",
-            "config": {"workload": WORKLOAD, "n": inst.n, "k": inst.k, "seed": inst.recipe.seed,
+            "config": {"workload": WORKLOAD if args.workload == "city" else
+                       "tiny ASRAL solve: |D|=2,000 x |S|=20 uniform points, CM int16",
+                       "n": inst.n, "k": inst.k, "seed": inst.recipe.seed,
                        "cluster_size": st1.cluster_size, "objective": objective,
-                       "l2": "inputs larger than L2 (200 MB CM)",
+                       "l2": "inputs larger than L2 (200 MB CM)" if args.workload == "city" else
+                             "CM fits L2 (small configuration)",
                        "max_rounds": args.max_rounds,
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": steps,
