@@ -71,6 +71,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(ms: float, world: int, device="cuda") -> float:
+    """The slowest rank's time (replicas: every rank did the same work)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, steps: int, ms: float) -> float:
+    """Whole-job solves/s: every rank solved `steps` instances in at most ms."""
+    return world * steps / (ms / 1000.0)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -287,13 +303,9 @@ def run_ours(args):
     if objective is None:
         objective = solver.objective
     assert solver.objective == objective, "solves are not deterministic"
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1000.0)
+    value = replica_value(world, args.steps, ms)
 
     # algorithmic CM bytes of one solve (= one launch); every step resets the
     # counters, so st1 holds the last timed solve alone
@@ -765,8 +777,11 @@ def run_road(args):
 
 def main():
     args = parse()
+    rank, world, _ = dist_env()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload not in ("city", "tiny") and world > 1 and rank != 0:
+        return   # the batch / serve / large / road measurements run on rank 0 only
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "serve":
