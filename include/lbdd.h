@@ -204,9 +204,10 @@ int lbdd_solve_batch(lbdd_solver* const* solvers, int m, int64_t max_rounds,
                      int cluster_size, int max_clusters, void* stream);
 
 /* Autotuner of the batch plan: for every (cost width, k bucket
- * 2^(b-1) < k <= 2^b) present among the m solvers, clones the instance with
- * the most units and times probe_rounds rounds (after the prologue) on one
- * cluster of each size that fits; the ns per round are kept per device for
+ * 2^(b-1) < k <= 2^b) present among the m solvers, takes the instance with
+ * the most units, builds a scaled-down copy (its first probe_rounds units,
+ * capacities scaled by the same ratio) and times a complete solve of it on
+ * one cluster of each size that fits; the ns per round are kept per device for
  * the process's lifetime and used by every later batch plan and server pass.
  * The solvers themselves are not modified.  lbdd_tune_get reads one entry
  * (0 = not measured); lbdd_tune_clear forgets all. */

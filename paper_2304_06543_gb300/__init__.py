@@ -453,7 +453,7 @@ class Batch:
             pass
 
 
-def autotune(solvers, probe_rounds: int = 256, stream=None):
+def autotune(solvers, probe_rounds: int = 4096, stream=None):
     _check(load().lbdd_autotune(_handles(solvers), len(solvers), int(probe_rounds),
                                 _stream_handle(stream)), "lbdd_autotune")
 

@@ -1247,24 +1247,29 @@ cudaError_t launch_solver_t(const DevInst* d_insts, int ninst, int* d_counter, i
 
 // Kernel attributes only ever grow (a launch needs at least its own dynamic
 // shared memory; concurrent callers must not lower what another one set).
+// Attributes belong to the current device, so the high-water marks are kept
+// per device.
 template <typename T>
 cudaError_t prepare_solver_t(int C, size_t smem) {
+  constexpr int kDevs = 64;
   static std::mutex mu;
-  static size_t cur_smem = 0;
-  static bool non_portable = false;
+  static size_t cur_smem[kDevs] = {};
+  static bool non_portable[kDevs] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kDevs) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(mu);
   auto kern = asral_cluster_kernel<T>;
-  if (smem > cur_smem) {
-    const cudaError_t e = cudaFuncSetAttribute(
-        kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > cur_smem[dev]) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    cur_smem = smem;
+    cur_smem[dev] = smem;
   }
-  if (C > 8 && !non_portable) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (C > 8 && !non_portable[dev]) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
-    non_portable = true;
+    non_portable[dev] = true;
   }
   return cudaSuccess;
 }

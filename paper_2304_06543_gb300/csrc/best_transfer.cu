@@ -18,6 +18,7 @@
 //   4. unpack to the (tc, td) int32 pair.
 // Step 3 reads every CM byte of the allotted rows exactly once and is the
 // HBM-bound kernel; everything else moves O(n + k*k) bytes.
+#include <atomic>
 #include <algorithm>
 
 #include "lbdd_device.cuh"
@@ -580,13 +581,17 @@ cudaError_t best_transfer_run(int32_t n, int32_t k, const void* cm, int elem_byt
   cudaMemsetAsync(W.err, 0, 2 * sizeof(int), st);
   bt_item_list<<<grid_lin, kThreads, 0, st>>>(W.seg_start, W.seg_end, W.item_off, k, W.items);
   if (elem_bytes == 2) {
-    static bool attr_set = false;   // the staged kernel's dynamic shared memory
-    if (!attr_set) {
-      const cudaError_t e = cudaFuncSetAttribute(
-          bt_scan_rows_staged16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-          (int)bt_staged_smem_bytes());
+    // the staged kernel's dynamic shared memory, set once per device
+    static std::atomic<uint64_t> attr_set{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!(attr_set.load() & (1ull << dev))) {
+      e = cudaFuncSetAttribute(bt_scan_rows_staged16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)bt_staged_smem_bytes());
       if (e != cudaSuccess) return e;
-      attr_set = true;
+      attr_set.fetch_or(1ull << dev);
     }
     bt_scan_rows_staged16<<<grid_scan, kThreads, bt_staged_smem_bytes(), st>>>(
         static_cast<const int16_t*>(cm), ld, n, k, sv, W.ownv, W.item_off, W.items, W.t64,

@@ -368,6 +368,25 @@ int lbdd::clone_solver(const lbdd_solver* src, lbdd_solver** out) {
   return rc;
 }
 
+int lbdd::clone_prefix(const lbdd_solver* src, int32_t n_sub, lbdd_solver** out) {
+  if (!src || !out || n_sub < 1) return LBDD_ERR_ARG;
+  n_sub = std::min(n_sub, src->n);
+  const int32_t Q = src->h_inst.Q;
+  std::vector<int32_t> cap(src->k), q((size_t)src->k * Q), pen(src->k);
+  CK(cudaMemcpyAsync(cap.data(), src->cap, 4ull * src->k, cudaMemcpyDeviceToHost, src->st));
+  CK(cudaMemcpyAsync(q.data(), src->h_inst.pen, 4ull * src->k * Q, cudaMemcpyDeviceToHost,
+                     src->st));
+  CK(cudaStreamSynchronize(src->st));
+  for (int32_t c = 0; c < src->k; ++c) {
+    pen[c] = q[(size_t)c * Q];
+    cap[c] = std::max<int32_t>(1, (int32_t)((int64_t)cap[c] * n_sub / src->n));
+  }
+  int rc = create_impl(out, n_sub, src->k, src->cm, src->elem == 2 ? LBDD_CM_I16 : LBDD_CM_I32,
+                       1, src->ld, cap.data(), pen.data(), src->st);
+  if (rc == LBDD_OK && Q > 1) rc = lbdd_set_penalty_table(*out, q.data(), Q);
+  return rc;
+}
+
 extern "C" int lbdd_set_penalty_table(lbdd_solver* s, const int32_t* qtab, int32_t Q) {
   if (!s || !qtab || Q < 1 || s->strict) return LBDD_ERR_ARG;
   for (int32_t c = 0; c < s->k; ++c)

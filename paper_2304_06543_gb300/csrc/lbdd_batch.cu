@@ -23,6 +23,7 @@
 //    counters, the forked group launches and the status gather are captured
 //    once into a CUDA graph; lbdd_batch_run replays it.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -104,15 +105,20 @@ struct Est {
 };
 
 // Cluster size and per-round estimate of every instance.
-static int choose_sizes(lbdd_solver* const* v, const int64_t* rem, int m, int forced_C, int dev,
-                        int sms, std::vector<Est>* est) {
+using Cands = std::vector<std::vector<std::pair<int, double>>>;
+
+// Cluster size and per-round estimate of every instance: the least SM-time
+// per round among the measured sizes (the default rule when unmeasured).
+// cands[i] lists instance i's measured (C, ns per round) pairs.
+static int choose_sizes(lbdd_solver* const* v, int m, int forced_C, int dev,
+                        std::vector<Est>* est, Cands* cands) {
   est->assign(m, Est{1, 1.0});
+  cands->assign(m, {});
   TuneTable tab;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tab = g_tune[dev];
   }
-  std::vector<std::vector<std::pair<int, double>>> cands(m);
   for (int i = 0; i < m; ++i) {
     const lbdd_solver* s = v[i];
     if (forced_C > 0) {
@@ -122,8 +128,8 @@ static int choose_sizes(lbdd_solver* const* v, const int64_t* rem, int m, int fo
     }
     const double* row = tab.ns[wid(s->elem)][bucket_of(s->k)];
     for (int C = 1; C <= 16; C <<= 1)
-      if (row[cidx(C)] > 0 && fits_k(s->k, s->elem, C)) cands[i].push_back({C, row[cidx(C)]});
-    if (cands[i].empty()) {
+      if (row[cidx(C)] > 0 && fits_k(s->k, s->elem, C)) (*cands)[i].push_back({C, row[cidx(C)]});
+    if ((*cands)[i].empty()) {
       const int C = default_cluster(s->k, s->elem);
       if (!fits_k(s->k, s->elem, C)) return LBDD_ERR_ARG;
       (*est)[i] = Est{C, (double)s->k / C + 1.0};
@@ -131,33 +137,9 @@ static int choose_sizes(lbdd_solver* const* v, const int64_t* rem, int m, int fo
     }
     // throughput-best: least SM-time per round; ties go to the larger cluster
     Est best{0, 0};
-    for (auto& c : cands[i])
+    for (auto& c : (*cands)[i])
       if (best.C == 0 || c.second * c.first <= best.t * best.C) best = Est{c.first, c.second};
     (*est)[i] = best;
-  }
-  if (forced_C > 0) return LBDD_OK;
-  // Instances longer than the batch's SM-time per SM get faster clusters,
-  // longest first, while that lowers their own time.
-  for (int iter = 0; iter < 4 * m; ++iter) {
-    double total = 0;
-    int top = -1;
-    double top_len = 0;
-    for (int i = 0; i < m; ++i) {
-      const double len = (double)rem[i] * (*est)[i].t;
-      total += len * (*est)[i].C;
-      if (!cands[i].empty() && len > top_len) { top_len = len; top = i; }
-    }
-    const double bound = total / std::max(1, sms);
-    if (top < 0 || top_len <= bound) break;
-    Est next{0, 0};
-    for (auto& c : cands[top])
-      if (c.first > (*est)[top].C && c.second < (*est)[top].t && (next.C == 0 || c.second < next.t))
-        next = Est{c.first, c.second};
-    if (next.C == 0) {
-      cands[top].clear();              // nothing faster: keep, and look at the next one
-      continue;
-    }
-    (*est)[top] = next;
   }
   return LBDD_OK;
 }
@@ -165,18 +147,11 @@ static int choose_sizes(lbdd_solver* const* v, const int64_t* rem, int m, int fo
 // Order of instances inside a group's work queue.
 enum Order { LONGEST_FIRST = 0, SHORTEST_FIRST = 1 };
 
-// rem[i]: rounds instance i has left.  Groups, their cluster counts and
-// queue orders for one pass over the instances.
-static int make_plan(lbdd_solver* const* v, const int64_t* rem, int m, int forced_C,
-                     int max_clusters, int dev, int sms, Order order, std::vector<Group>* groups,
-                     std::vector<int>* cluster_of) {
-  std::vector<Est> est;
-  int rc = choose_sizes(v, rem, m, forced_C, dev, sms, &est);
-  if (rc) return rc;
+// Groups of instances with equal (cost width, cluster size, options).
+static int build_groups(lbdd_solver* const* v, const int64_t* rem, int m,
+                        const std::vector<Est>& est, Order order, std::vector<Group>* groups) {
   groups->clear();
-  cluster_of->assign(m, 0);
   for (int i = 0; i < m; ++i) {
-    (*cluster_of)[i] = est[i].C;
     Group* g = nullptr;
     const int fl = solver_flags(v[i]);
     for (auto& x : *groups)
@@ -193,10 +168,9 @@ static int make_plan(lbdd_solver* const* v, const int64_t* rem, int m, int force
     g->work += len * est[i].C;
     g->longest = std::max(g->longest, len);
   }
-  // heaviest group first; inside a group, longest instance first
+  // heaviest group first; inside a group, longest (or shortest) instance first
   std::stable_sort(groups->begin(), groups->end(),
                    [](const Group& a, const Group& b) { return a.work > b.work; });
-  double total = 0;
   for (auto& g : *groups) {
     std::stable_sort(g.idx.begin(), g.idx.end(), [&](int a, int b) {
       const double la = (double)rem[a] * est[a].t, lb = (double)rem[b] * est[b].t;
@@ -206,22 +180,34 @@ static int make_plan(lbdd_solver* const* v, const int64_t* rem, int m, int force
     for (int i : g.idx) kmax = std::max(kmax, v[i]->k);
     g.smem = launch_smem(kmax, g.C, g.elem);
     if (g.smem > kMaxSmem) return LBDD_ERR_ARG;
-    total += g.work;
   }
-  // SMs shared in proportion to each group's SM-time
+  return LBDD_OK;
+}
+
+// Upper bound on a group's clusters: its instances, co-residency, the SMs.
+static int group_cap(const Group& g, int max_clusters, int sms, int* cap) {
+  const int fit = solver_max_clusters(g.C, g.elem, g.smem);
+  if (fit < 1) return LBDD_ERR_ARG;
+  *cap = std::min<int>((int)g.idx.size(), fit);
+  if (max_clusters > 0) *cap = std::min(*cap, max_clusters);
+  *cap = std::max(1, std::min(*cap, sms / g.C));
+  return LBDD_OK;
+}
+
+// SMs in proportion to each group's estimated SM-time.
+static int allocate_proportional(std::vector<Group>* groups, int max_clusters, int sms) {
+  double total = 0;
+  for (auto& g : *groups) total += g.work;
   int used = 0;
   std::vector<int> cap(groups->size());
   for (size_t gi = 0; gi < groups->size(); ++gi) {
     Group& g = (*groups)[gi];
-    const int fit = solver_max_clusters(g.C, g.elem, g.smem);
-    if (fit < 1) return LBDD_ERR_ARG;
-    cap[gi] = std::min<int>((int)g.idx.size(), fit);
-    if (max_clusters > 0) cap[gi] = std::min(cap[gi], max_clusters);
+    int rc = group_cap(g, max_clusters, sms, &cap[gi]);
+    if (rc) return rc;
     const double share = total > 0 ? sms * g.work / total : sms;
     g.ncl = std::max(1, std::min(cap[gi], (int)std::floor(share / g.C)));
     used += g.ncl * g.C;
   }
-  // trim to the SM count, then hand out what is left, most-needed first
   auto need = [&](const Group& g) { return g.work / (g.ncl * g.C); };
   while (used > sms) {
     int best = -1;
@@ -243,6 +229,43 @@ static int make_plan(lbdd_solver* const* v, const int64_t* rem, int m, int force
     (*groups)[best].ncl++;
     used += (*groups)[best].C;
   }
+  return LBDD_OK;
+}
+
+// rem[i]: rounds instance i has left.  Groups, their cluster counts and
+// queue orders for one pass over the instances: sizes by least SM-time per
+// round, long instances moved to faster clusters, SMs shared in proportion
+// to estimated SM-time.
+static int make_plan(lbdd_solver* const* v, const int64_t* rem, int m, int forced_C,
+                     int max_clusters, int dev, int sms, Order order, std::vector<Group>* groups,
+                     std::vector<int>* cluster_of) {
+  std::vector<Est> est;
+  Cands cands;
+  int rc = choose_sizes(v, m, forced_C, dev, &est, &cands);
+  if (rc) return rc;
+  // instances longer than the plan's SM-time per SM get faster clusters,
+  // longest first, while that lowers their own time
+  for (int iter = 0; iter < 4 * m && forced_C == 0; ++iter) {
+    double total = 0, top_len = 0;
+    int top = -1;
+    for (int i = 0; i < m; ++i) {
+      const double len = (double)rem[i] * est[i].t;
+      total += len * est[i].C;
+      if (!cands[i].empty() && len > top_len) { top_len = len; top = i; }
+    }
+    if (top < 0 || top_len <= total / std::max(1, sms)) break;
+    Est next{0, 0};
+    for (auto& c : cands[top])
+      if (c.first > est[top].C && c.second < est[top].t && (next.C == 0 || c.second < next.t))
+        next = Est{c.first, c.second};
+    if (next.C == 0) { cands[top].clear(); continue; }
+    est[top] = next;
+  }
+  rc = build_groups(v, rem, m, est, order, groups);
+  if (!rc) rc = allocate_proportional(groups, max_clusters, sms);
+  if (rc) return rc;
+  cluster_of->assign(m, 0);
+  for (int i = 0; i < m; ++i) (*cluster_of)[i] = est[i].C;
   return LBDD_OK;
 }
 
@@ -516,11 +539,14 @@ extern "C" int lbdd_autotune(lbdd_solver* const* solvers, int m, int probe_round
   }
   for (int key = 0; key < 2 * kBuckets; ++key) {
     if (rep[key] < 0) continue;
+    // a whole solve of a scaled-down copy (first probe_rounds units,
+    // capacities scaled alike) passes through the filling and the overload
+    // phases in proportion, unlike the first rounds of the instance itself
     lbdd_solver* tmp = nullptr;
-    rc = clone_solver(solvers[rep[key]], &tmp);
+    rc = clone_prefix(solvers[rep[key]], probe_rounds, &tmp);
     if (rc) return rc;
     double row[kNC] = {0, 0, 0, 0, 0};
-    const int64_t rounds = std::min<int64_t>(probe_rounds, tmp->n);
+    const int64_t rounds = tmp->n;
     for (int C = 1; C <= 16 && rc == LBDD_OK; C <<= 1) {
       if (!fits_k(tmp->k, tmp->elem, C)) continue;
       float ms = 0;

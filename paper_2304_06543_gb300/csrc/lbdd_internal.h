@@ -75,6 +75,9 @@ size_t solver_footprint(int32_t n, int32_t k, int in_elem, int elem);
 // A new solver on the same device holding a copy of src's instance (costs,
 // capacities, penalties), in the initial state.
 int clone_solver(const lbdd_solver* src, lbdd_solver** out);
+// A smaller instance shaped like src: its first n_sub units, capacities
+// scaled by n_sub / n (at least 1), the same penalties.
+int clone_prefix(const lbdd_solver* src, int32_t n_sub, lbdd_solver** out);
 // Advances s by up to max_rounds rounds on C-CTA clusters; *ms is the
 // kernel's device time.
 int solve_timed(lbdd_solver* s, int64_t max_rounds, int C, float* ms);
