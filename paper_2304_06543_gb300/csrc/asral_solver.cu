@@ -673,7 +673,8 @@ struct Solver {
         uint64_t key = kNoKey;
         if (idx < nslots) {
           const int r = idx / w;
-          key = (uint64_t)dsmem_ld64(dsmem_addr(s_outbox + pb * obs + (idx - r * w), (uint32_t)r));
+          key = C == 1 ? s_outbox[pb * obs + idx]
+                       : (uint64_t)dsmem_ld64(dsmem_addr(s_outbox + pb * obs + (idx - r * w), (uint32_t)r));
         }
         const unsigned m = __ballot_sync(0xffffffffu, key != kNoKey);
         if (m != 0u) {

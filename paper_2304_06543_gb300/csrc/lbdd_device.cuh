@@ -121,6 +121,12 @@ __device__ __forceinline__ uint32_t cluster_count() {
 // Full cluster barrier; every thread of every CTA of the cluster must reach
 // it.  Release/acquire order shared and global memory across the cluster.
 __device__ __forceinline__ void cluster_sync_all() {
+  uint32_t nr;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(nr));
+  if (nr == 1) {   // a one-CTA cluster: the CTA barrier orders the same accesses
+    __syncthreads();
+    return;
+  }
   asm volatile(
       "barrier.cluster.arrive.release.aligned;\n\t"
       "barrier.cluster.wait.acquire.aligned;\n\t" ::: "memory");
