@@ -491,21 +491,25 @@ int lbdd::solve_timed(lbdd_solver* s, int64_t max_rounds, int C, float* ms) {
   if (rc) return rc;
   if (C < 1 || !fits(s, C)) return LBDD_ERR_ARG;
   const size_t smem = launch_smem(s->k, C, s->elem);
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  struct Events {   // destroyed on every return path
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Events() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  CK(cudaEventCreate(&ev.a));
+  CK(cudaEventCreate(&ev.b));
   CK(cudaMemsetAsync(s->counter, 0, sizeof(int32_t), s->st));
   CK(prepare_solver(C, s->elem, smem));
-  CK(cudaEventRecord(e0, s->st));
+  CK(cudaEventRecord(ev.a, s->st));
   CK(launch_solver(s->d_inst, 1, s->counter, C, 1, s->elem, smem, solver_flags(s), s->st, 0,
                    false));
-  CK(cudaEventRecord(e1, s->st));
+  CK(cudaEventRecord(ev.b, s->st));
   int64_t st = 0;
   CK(cudaMemcpyAsync(&st, s->ctl + CTL_STATUS, sizeof(int64_t), cudaMemcpyDeviceToHost, s->st));
   CK(cudaStreamSynchronize(s->st));
-  CK(cudaEventElapsedTime(ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  CK(cudaEventElapsedTime(ms, ev.a, ev.b));
   return status_to_rc(st);
 }
 
