@@ -266,7 +266,9 @@ int lbdd_server_poll(lbdd_server* srv, int64_t ticket, int64_t timeout_ms,
 int lbdd_server_release(lbdd_server* srv, int64_t ticket);
 int lbdd_server_get_stats(lbdd_server* srv, lbdd_server_stats* out);
 /* Stop: queued requests fail with LBDD_ERR_STATE, the pass in flight ends
- * at its quantum, everything is freed. */
+ * at its quantum, everything is freed (request records included).  No other
+ * call on the same server may be in progress or follow it: a thread still
+ * waiting in lbdd_server_poll would wait on freed state. */
 void lbdd_server_destroy(lbdd_server* srv);
 
 /* Tracked objective Delta of Alg. 2 (equals Eq. (1) of the current
