@@ -108,7 +108,11 @@ typedef enum lbdd_option {
 } lbdd_option;
 
 /* Create a solver for one LBDD instance (Section 2.1 inputs).
- *   n, k        : demand units and service centers, n >= 1, k >= 1.
+ *   n, k        : demand units and service centers, n >= 1, 1 <= k <= 4826
+ *                 (every CTA of a 16-CTA cluster keeps per-center label,
+ *                 hop, load, capacity and penalty replicas and a k + 1 key
+ *                 frontier in its 227 KB of shared memory; larger k returns
+ *                 LBDD_ERR_ARG).
  *   cm          : n*k entries, demand-major, every entry >= 1; dtype per
  *                 cm_dtype; host memory unless cm_is_device != 0.
  *                 int32 input whose maximum is below 32768 is stored as

@@ -83,3 +83,68 @@ def test_city_snapshot_sampled_rows(gpu_lib):
         exp_d = members[best]
         exp_t[u], exp_d[u] = 2**31 - 1, -1
         assert np.array_equal(tc[u], exp_t) and np.array_equal(td[u], exp_d)
+
+
+def _check_sampled_rows(inst, assign, tc, td, centers):
+    for u in centers:
+        members = np.nonzero(assign == u)[0]
+        if len(members) == 0:
+            assert (tc[u] == 2**31 - 1).all() and (td[u] == -1).all()
+            continue
+        rows = inst.cm[members].astype(np.int64)
+        t = rows - rows[:, [u]]
+        best = t.argmin(axis=0)               # first minimum: lowest d on equal cost
+        exp_t = t[best, np.arange(inst.k)]
+        exp_d = members[best]
+        exp_t[u], exp_d[u] = 2**31 - 1, -1
+        assert np.array_equal(tc[u], exp_t) and np.array_equal(td[u], exp_d)
+
+
+def _check_witnesses(inst, assign, tc, td):
+    """Every finite entry names a unit of its row's center whose transfer
+    costs exactly that much; every empty center's row is empty."""
+    k = inst.k
+    u, v = np.nonzero(td >= 0)
+    d = td[u, v]
+    assert (assign[d] == u).all() and (u != v).all()
+    cost = inst.cm[d, v].astype(np.int64) - inst.cm[d, u].astype(np.int64)
+    assert np.array_equal(cost, tc[u, v].astype(np.int64))
+    empty = np.bincount(assign[assign >= 0], minlength=k) == 0
+    assert (td[empty] == -1).all() and (tc[empty] == 2**31 - 1).all()
+    assert (np.diag(td) == -1).all()
+
+
+def test_large_snapshot_full_size(gpu_lib):
+    """The 2,000,000 x 2,000 instance at the size the scan benchmark times,
+    every unit at its s_min, int16 and int32 storage: the two tables are
+    equal, every entry's witness is consistent, and sampled rows equal the
+    definition (a plain loop over that center's units)."""
+    import torch
+    lb = gpu_lib
+    inst = L.make_named("large", dtype="i16")
+    n, k = inst.n, inst.k
+    smin = inst.cm.argmin(axis=1).astype(np.int32)    # first minimum: lowest center index
+    ld16, ld32 = lb.cm_pitch(k, lb.CM_I16), lb.cm_pitch(k, lb.CM_I32)
+    assert ld16 == k and ld32 == k                     # unpadded rows: one host copy serves both
+    cm16 = torch.zeros(n * k + 128, dtype=torch.int16, device="cuda")
+    cm16[: n * k].copy_(torch.from_numpy(inst.cm.reshape(-1)))
+    a = torch.from_numpy(smin).cuda()
+    wsb = lb.best_transfer_workspace(n, k)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+
+    def table(buf, cmd):
+        tc = torch.empty(k * k, dtype=torch.int32, device="cuda")
+        td = torch.empty(k * k, dtype=torch.int32, device="cuda")
+        lb.best_transfer(n, k, buf, cmd, k, a, tc, td, ws, wsb)
+        torch.cuda.synchronize()
+        return tc.cpu().numpy().reshape(k, k), td.cpu().numpy().reshape(k, k)
+
+    tc, td = table(cm16, lb.CM_I16)
+    cm32 = cm16.to(torch.int32)
+    del cm16
+    tc32, td32 = table(cm32, lb.CM_I32)
+    del cm32
+    assert np.array_equal(tc, tc32) and np.array_equal(td, td32)
+    _check_witnesses(inst, smin, tc, td)
+    rng = np.random.default_rng(3)
+    _check_sampled_rows(inst, smin, tc, td, rng.choice(k, 16, replace=False))

@@ -223,3 +223,25 @@ def test_large_prefix_matches_golden(gpu_lib):
         assert s.objective == gold["delta"]
         assert sha(s.assignment().astype(np.int32)) == gold["assign_sha256"]
         assert sha(s.loads().astype(np.int64)) == gold["load_sha256"]
+
+
+def test_largest_k(gpu_lib):
+    """k = 4,826, the most centers a 16-CTA cluster's shared memory holds
+    (label, hop, load, capacity and penalty replicas plus the frontier of
+    k + 1 keys per CTA): a prefix of the solve and the best-transfer table
+    after it equal the oracle's; one more center is refused at creation."""
+    k = 4826
+    inst = L.make(L.Recipe(n=4900, k=k, seed=4826, cap_frac=0.99, pen=(1, 30), name="maxk"))
+    R = 12
+    ref = oracle.asral(inst.cm, inst.cap, inst.pen, max_rounds=R)
+    assert ref.rc == 0
+    assign, delta, loads, st, (tc, td) = run_gpu(gpu_lib, inst.cm, inst.cap, inst.pen, rounds=R)
+    assert st.cluster_size == 16
+    assert_same((assign, delta, loads, st, None), ref, k)
+    tc_ref, td_ref = oracle.best_transfer(inst.cm, ref.assign)
+    tc_ref = np.where(tc_ref >= oracle.INF, 2**31 - 1, tc_ref)
+    assert np.array_equal(tc, tc_ref) and np.array_equal(td, td_ref)
+    wide = np.ones((8, k + 1), np.int32)
+    with pytest.raises(gpu_lib.LbddError) as e:
+        gpu_lib.Solver(wide, np.ones(k + 1, np.int32), np.ones(k + 1, np.int32))
+    assert e.value.code == gpu_lib.ERR_ARG
