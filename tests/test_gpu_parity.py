@@ -245,3 +245,21 @@ def test_largest_k(gpu_lib):
     with pytest.raises(gpu_lib.LbddError) as e:
         gpu_lib.Solver(wide, np.ones(k + 1, np.int32), np.ones(k + 1, np.int32))
     assert e.value.code == gpu_lib.ERR_ARG
+
+
+@pytest.mark.parametrize("n,k,cm_max,cap_frac", [
+    (1, 1, 5, 0.5),      # one unit, one center
+    (1, 7, 9, 0.5),      # one unit: Delta is its cheapest cost
+    (40, 1, 9, 0.1),     # one center, overloaded from the fifth unit on
+    (200, 9, 1, 0.5),    # every cost equal: only the tie-break rules decide
+    (64, 64, 2, 1.0),    # capacity exactly n, one slot per center
+    (129, 33, 4, 0.2),   # ragged: 33 columns over 1, 2 and 4 CTAs
+])
+def test_degenerate_instances(gpu_lib, n, k, cm_max, cap_frac):
+    inst = L.random_small(9100 + n + k, n=n, k=k, cm_max=cm_max, cap_frac=cap_frac, pen=(1, 9))
+    ref = oracle.asral(inst.cm, inst.cap, inst.pen)
+    assert ref.rc == 0
+    assert ref.delta == oracle.objective(inst.cm, inst.cap, inst.pen, ref.assign)
+    for cluster in sorted({1, min(2, k), min(4, k)}):
+        out = run_gpu(gpu_lib, inst.cm, inst.cap, inst.pen, cluster=cluster)
+        assert_same(out, ref, k)
