@@ -152,3 +152,42 @@ def test_full_batched_mix_matches_oracle_golden(gpu_lib):
     finally:
         for s in solvers:
             s.close()
+
+
+def test_mixed_variants_in_one_batch(gpu_lib):
+    """Strict-LBDD solvers (their own launch group), solvers with penalty
+    tables and plain solvers in one batch, in slices: each ends with its own
+    oracle's result."""
+    plain = mix(4, seed0=40)
+    strict = [L.random_small(9700 + i, n=[60, 150][i % 2], k=[5, 12][i % 2], cm_max=25,
+                             cap_frac=[0.7, 1.3][i % 2]) for i in range(3)]
+    tabled = [L.random_small(9800 + i, n=120, k=[6, 17][i % 2], cm_max=30, cap_frac=0.5)
+              for i in range(3)]
+    qs = [L.penalty_table(9800 + i, x.k, 7, base=(1, 40), step=(0, 15)) for i, x in enumerate(tabled)]
+    solvers, expect = [], []
+    try:
+        for x in plain:
+            ref = oracle.asral(x.cm, x.cap, x.pen)
+            solvers.append(gpu_lib.Solver(x.cm, x.cap, x.pen))
+            expect.append((ref.delta, ref.assign))
+        for x in strict:
+            rc, a, cost, _ = oracle.strict(x.cm, x.cap)
+            assert rc == 0
+            solvers.append(gpu_lib.Solver(x.cm, x.cap, None, strict=True))
+            expect.append((cost, a))
+        for x, q in zip(tabled, qs):
+            ref = oracle.asral_q(x.cm, x.cap, q)
+            solvers.append(gpu_lib.Solver(x.cm, x.cap, x.pen, qtab=q))
+            expect.append((ref.delta, ref.assign))
+        order = [solvers[i] for i in (4, 0, 7, 1, 5, 2, 8, 3, 6)]   # interleaved
+        b = gpu_lib.Batch(order)
+        for _ in range(3):
+            b.run(40)
+        b.run()
+        b.close()
+        for s, (delta, assign) in zip(solvers, expect):
+            assert s.objective == delta
+            assert np.array_equal(s.assignment(), assign)
+    finally:
+        for s in solvers:
+            s.close()
