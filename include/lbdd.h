@@ -108,10 +108,8 @@ typedef enum lbdd_option {
 } lbdd_option;
 
 /* Create a solver for one LBDD instance (Section 2.1 inputs).
- *   n, k        : demand units and service centers, n >= 1, 1 <= k <= 4826
- *                 (every CTA of a 16-CTA cluster keeps per-center label,
- *                 hop, load, capacity and penalty replicas and a k + 1 key
- *                 frontier in its 227 KB of shared memory; larger k returns
+ *   n, k        : demand units and service centers, n >= 1,
+ *                 1 <= k <= lbdd_max_centers() (4,800; larger k returns
  *                 LBDD_ERR_ARG).
  *   cm          : n*k entries, demand-major, every entry >= 1; dtype per
  *                 cm_dtype; host memory unless cm_is_device != 0.
@@ -124,6 +122,14 @@ typedef enum lbdd_option {
  * is set to NULL on failure. */
 int lbdd_create(lbdd_solver** out, int32_t n, int32_t k, const void* cm, int cm_dtype,
                 int cm_is_device, const int32_t* cap, const int32_t* pen, void* cuda_stream);
+
+/* The most service centers a solver accepts: every CTA of a 16-CTA cluster
+ * keeps per-center label, hop, load, capacity and penalty replicas and a
+ * frontier of k + 1 keys in its shared memory (at most 227 KB, of which the
+ * kernel's static variables take a little).  A strict-LBDD instance whose
+ * capacities sum below n counts its dummy center too.  Host arithmetic; no
+ * device needed. */
+int32_t lbdd_max_centers(void);
 
 /* Set an lbdd_option; LBDD_ERR_ARG for an unknown option or bad value. */
 int lbdd_set_option(lbdd_solver* s, int option, int64_t value);

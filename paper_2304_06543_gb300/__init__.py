@@ -108,6 +108,8 @@ def load():
         lib.lbdd_best_transfer_workspace.restype = sz
         lib.lbdd_best_transfer.argtypes = [i32, i32, P, c_int, i64, P, P, P, P, sz, P]
         lib.lbdd_cm_pitch.argtypes = [i32, c_int]
+        lib.lbdd_max_centers.argtypes = []
+        lib.lbdd_max_centers.restype = i32
         lib.lbdd_cm_pitch.restype = i64
         lib.lbdd_solver_cm.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(c_int),
                                        ctypes.POINTER(i64)]
@@ -314,6 +316,11 @@ def solver_cm(h):
 
 def cm_pitch(k: int, cm_dtype: int) -> int:
     return int(load().lbdd_cm_pitch(k, cm_dtype))
+
+
+def max_centers() -> int:
+    """lbdd_max_centers: the largest k a solver accepts."""
+    return int(load().lbdd_max_centers())
 
 
 def best_transfer_workspace(n: int, k: int) -> int:

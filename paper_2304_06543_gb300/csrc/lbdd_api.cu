@@ -19,6 +19,9 @@ static std::mutex g_err_mu;
 int lbdd::cuda_fail(cudaError_t e, const char* what) {
   std::lock_guard<std::mutex> lk(g_err_mu);
   snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", what, cudaGetErrorString(e));
+  // the failure is reported here: clear the thread's last-error state, so that
+  // the launch check of a later call does not report it a second time
+  (void)cudaGetLastError();
   return e == cudaErrorMemoryAllocation ? LBDD_ERR_OOM : LBDD_ERR_CUDA;
 }
 
@@ -185,7 +188,29 @@ bool lbdd::fits_k(int32_t k, int elem, int C) {
   if (smem > kMaxSmem) return false;
   const int32_t w = (k + C - 1) / C;
   if (w > solver_max_k(1, elem)) return false;
-  return solver_max_clusters(C, elem, smem) >= 1;
+  if (solver_max_clusters(C, elem, smem) >= 1) return true;
+  // a refused attribute or occupancy query only means "does not fit": clear
+  // the error it left, which a later launch check would otherwise report
+  (void)cudaGetLastError();
+  return false;
+}
+
+// Largest k whose 16-CTA launch fits kMaxSmem for both stored CM widths
+// (the replicas and the frontier grow with k; the cost slice then lives in
+// global memory).  Host arithmetic only.
+extern "C" int32_t lbdd_max_centers(void) {
+  int32_t best = 65535;
+  for (int elem = 2; elem <= 4; elem += 2) {
+    int32_t lo = 1, hi = 65535;    // launch_smem(lo) fits; find the last k that does
+    if (launch_smem(lo, 16, elem) > kMaxSmem) return 0;
+    while (lo < hi) {
+      const int32_t mid = lo + (hi - lo + 1) / 2;
+      if (launch_smem(mid, 16, elem) <= kMaxSmem) lo = mid;
+      else hi = mid - 1;
+    }
+    best = std::min(best, lo);
+  }
+  return best;
 }
 
 static int fits(const lbdd_solver* s, int C) { return fits_k(s->k, s->elem, C) ? 1 : 0; }

@@ -187,7 +187,10 @@ static int build_groups(lbdd_solver* const* v, const int64_t* rem, int m,
 // Upper bound on a group's clusters: its instances, co-residency, the SMs.
 static int group_cap(const Group& g, int max_clusters, int sms, int* cap) {
   const int fit = solver_max_clusters(g.C, g.elem, g.smem);
-  if (fit < 1) return LBDD_ERR_ARG;
+  if (fit < 1) {
+    (void)cudaGetLastError();   // the refused query's error is reported as LBDD_ERR_ARG
+    return LBDD_ERR_ARG;
+  }
   *cap = std::min<int>((int)g.idx.size(), fit);
   if (max_clusters > 0) *cap = std::min(*cap, max_clusters);
   *cap = std::max(1, std::min(*cap, sms / g.C));

@@ -26,7 +26,10 @@ cudaError_t best_transfer_run(int32_t n, int32_t k, const void* cm, int elem_byt
                               const int32_t* assign, int32_t* tc, int32_t* td, void* ws,
                               cudaStream_t st, int num_sms);
 
-constexpr size_t kMaxSmem = 227 * 1024;   // dynamic shared memory a CTA may use
+// Dynamic shared memory a solver CTA may request: the 227 KB a block may
+// opt into, less 1 KB for the kernel's static shared variables (400 bytes
+// at present), which count against the same limit.
+constexpr size_t kMaxSmem = 227 * 1024 - 1024;
 }  // namespace lbdd
 
 struct lbdd_solver {

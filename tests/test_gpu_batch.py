@@ -179,7 +179,7 @@ def test_mixed_variants_in_one_batch(gpu_lib):
             ref = oracle.asral_q(x.cm, x.cap, q)
             solvers.append(gpu_lib.Solver(x.cm, x.cap, x.pen, qtab=q))
             expect.append((ref.delta, ref.assign))
-        order = [solvers[i] for i in (4, 0, 7, 1, 5, 2, 8, 3, 6)]   # interleaved
+        order = [solvers[i] for i in (4, 0, 7, 1, 5, 9, 2, 8, 3, 6)]   # interleaved
         b = gpu_lib.Batch(order)
         for _ in range(3):
             b.run(40)

@@ -226,11 +226,13 @@ def test_large_prefix_matches_golden(gpu_lib):
 
 
 def test_largest_k(gpu_lib):
-    """k = 4,826, the most centers a 16-CTA cluster's shared memory holds
-    (label, hop, load, capacity and penalty replicas plus the frontier of
-    k + 1 keys per CTA): a prefix of the solve and the best-transfer table
-    after it equal the oracle's; one more center is refused at creation."""
-    k = 4826
+    """k = lbdd_max_centers(), the most centers a 16-CTA cluster's shared
+    memory holds (label, hop, load, capacity and penalty replicas plus the
+    frontier of k + 1 keys per CTA): a prefix of the solve and the
+    best-transfer table after it equal the oracle's; one more center is
+    refused at creation."""
+    k = gpu_lib.max_centers()
+    assert k == 4800
     inst = L.make(L.Recipe(n=4900, k=k, seed=4826, cap_frac=0.99, pen=(1, 30), name="maxk"))
     R = 12
     ref = oracle.asral(inst.cm, inst.cap, inst.pen, max_rounds=R)

@@ -155,6 +155,13 @@ def test_scan_and_road_arguments_are_validated(lb, lib):
     assert lib.lbdd_road_cm(4, None, a16, a16, 1, a16, 1, a16, a16, 1, None) == lb.ERR_ARG
 
 
+def test_max_centers(lb):
+    """The k limit is host arithmetic over the solver's shared-memory layout:
+    below the 227 KB a CTA may use, whatever the stored CM width."""
+    k = lb.max_centers()
+    assert 4000 <= k <= 4826
+
+
 def test_tune_table_arguments(lb, lib):
     d = ctypes.c_double()
     for C in (0, 3, 32):
