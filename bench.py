@@ -169,15 +169,17 @@ def kernel_source_hash(files=None) -> str:
     return h.hexdigest()[:16]
 
 
-def committed_traffic(kernel: str):
+def committed_traffic(kernel: str, workload: str = "city"):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the kernel's current sources (the files listed with it), else None."""
+    the kernel's current sources (the files listed with it) and on this
+    workload, else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             t = json.load(f)
         e = t[kernel]
-        if e.get("source_hash") == kernel_source_hash(e.get("sources")):
+        if (e.get("workload") == workload and
+                e.get("source_hash") == kernel_source_hash(e.get("sources"))):
             return e
     except Exception:
         pass
@@ -200,8 +202,9 @@ def cpu_baseline(inst, rounds: int):
     dt = time.perf_counter() - t0
     assert res.rc == 0
     rps = rounds / dt
-    return {"value": rps / inst.n, "unit": "solves/s (extrapolated)", "cores": 1,
-            "kind": "oracle",
+    whole = rounds >= inst.n
+    return {"value": rps / inst.n, "unit": "solves/s" if whole else "solves/s (extrapolated)",
+            "cores": 1, "kind": "oracle",
             "sample": f"first {rounds} of {inst.n} rounds, heap mode, {dt:.1f} s; "
                       f"{rps:.1f} rounds/s",
             "rounds_per_s": rps, "seconds": dt}
@@ -252,7 +255,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def scan_roofline(lb, inst, hbm_peak, peak_kind):
+def scan_roofline(lb, inst, hbm_peak, peak_kind, name="city"):
     """Standalone best-transfer scan on the s_min snapshot (every unit at its
     most suitable center): bytes = n*k*2 (CM) + 4n (allotment)."""
     import torch
@@ -283,7 +286,9 @@ def scan_roofline(lb, inst, hbm_peak, peak_kind):
     return {"kernel": "lbdd_best_transfer (all stages)", "bound": "hbm", "achieved": gbs,
             "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
             "peak_kind": peak_kind, "ms": ms, "bytes": byts,
-            "config": "s_min allotment of the city instance, CM > L2 (200 MB)"}
+            "config": f"s_min allotment of the {name} instance ({n:,} x {k:,}), CM "
+                      f"{'larger' if n * k * 2 > 129e6 else 'smaller'} than L2 "
+                      f"({n * k * 2 / 1e6:.1f} MB)"}
 
 
 def run_ours(args):
@@ -344,7 +349,9 @@ def run_ours(args):
     rows_full = (dstat("rows_scanned") + 2 * inst.n * steps)     # rescans + prologue + merges
     alg_bytes = (rows_full * inst.k * w + dstat("col_rows") * 2 * w) / steps
     achieved = alg_bytes / (ms_per_step / 1000.0) / 1e9
-    traffic = committed_traffic("asral_cluster_kernel")
+    # the committed figure is for whole solves of its own workload
+    traffic = (committed_traffic("asral_cluster_kernel", args.workload)
+               if args.max_rounds < 0 else None)
     roofline = {"kernel": "asral_cluster_kernel", "bound": "hbm", "achieved": achieved,
                 "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "peak_kind": peak_kind,
@@ -386,7 +393,7 @@ def run_ours(args):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "steps": args.e2e_steps}
 
-    scan = None if args.no_scan else scan_roofline(lb, inst, hbm_peak, peak_kind)
+    scan = None if args.no_scan else scan_roofline(lb, inst, hbm_peak, peak_kind, args.workload)
     cpu = None if (args.no_cpu or rank != 0) else cpu_baseline(inst, args.cpu_rounds)
     if rank == 0:
         line = {

@@ -75,12 +75,13 @@ def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
 
 
 def test_traffic_entry_follows_its_sources():
-    """A committed DRAM-traffic figure is used only while the sources it was
-    captured on are unchanged."""
+    """A committed DRAM-traffic figure is used only for its own workload and
+    while the sources it was captured on are unchanged."""
     with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
         t = json.load(f)
     for name, e in t.items():
         current = bench.kernel_source_hash(e.get("sources")) == e["source_hash"]
-        got = bench.committed_traffic(name)
+        got = bench.committed_traffic(name, e["workload"])
         assert (got is not None) == current
+        assert bench.committed_traffic(name, e["workload"] + "-other") is None
     assert bench.committed_traffic("no_such_kernel") is None
