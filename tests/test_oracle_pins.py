@@ -138,6 +138,77 @@ def test_smin_and_order_definition():
     assert np.array_equal(order, np.lexsort((np.arange(J.n), cost)))
 
 
+# ---------------------------------------------------- best transfers -----
+
+def _best_transfer_certificate(cm, assign, tc, td):
+    """The facts that fix the table of Defs. 8-10 uniquely, checked as a
+    certificate rather than recomputed: every finite entry (u, v) names a
+    unit d allotted to u whose transfer cost CM(d, v) - CM(d, u) is the
+    entry (attained), no unit of u transfers to v for less (minimal), no unit
+    of u with a lower index transfers for the same cost (lowest d on ties);
+    a center without units, and the diagonal, have no entries."""
+    k = cm.shape[1]
+    cm = cm.astype(np.int64)
+    for u in range(k):
+        members = np.nonzero(assign == u)[0]
+        for v in range(k):
+            if u == v or len(members) == 0:
+                assert tc[u, v] >= oracle.INF and td[u, v] == -1
+                continue
+            d = int(td[u, v])
+            assert assign[d] == u and tc[u, v] == cm[d, v] - cm[d, u]
+            t = cm[members, v] - cm[members, u]
+            assert (t >= tc[u, v]).all()
+            assert not (members[t == tc[u, v]] < d).any()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_best_transfer_table_certificate(seed):
+    J = small(1750 + seed, [60, 200, 31, 120][seed], [4, 9, 13, 6][seed],
+              cm_max=[3, 20, 7, 50][seed])
+    rng = np.random.default_rng(seed)
+    assign = rng.integers(-1, J.k, J.n).astype(np.int32)     # -1: not allotted yet
+    assign[assign == 1] = 0                                  # center 1 holds nothing
+    tc, td = oracle.best_transfer(J.cm, assign)
+    _best_transfer_certificate(J.cm, assign, tc, td)
+
+
+def test_best_transfer_certificate_rejects_plausible_mistakes():
+    """The certificate fails for a transposed table, a flipped sign and the
+    highest instead of the lowest d on ties."""
+    J = small(1760, 150, 7, cm_max=4)
+    assign = np.argmin(J.cm, axis=1).astype(np.int32)
+    tc, td = oracle.best_transfer(J.cm, assign)
+    _best_transfer_certificate(J.cm, assign, tc, td)
+    cm = J.cm.astype(np.int64)
+    k = J.k
+    flipped = tc.copy()
+    fin = td >= 0
+    u, v = np.nonzero(fin)
+    flipped[u, v] = cm[td[u, v], u] - cm[td[u, v], v]
+    last = td.copy()
+    for a in range(k):
+        members = np.nonzero(assign == a)[0]
+        for b in range(k):
+            if a != b and len(members):
+                t = cm[members, b] - cm[members, a]
+                last[a, b] = members[np.nonzero(t == t.min())[0][-1]]
+    for bad_tc, bad_td in ((tc.T.copy(), td.T.copy()), (flipped, td), (tc, last)):
+        with pytest.raises(AssertionError):
+            _best_transfer_certificate(J.cm, assign, bad_tc, bad_td)
+
+
+def test_best_transfer_at_smin_is_nonnegative():
+    """With every unit at its most suitable center (Alg. 2, first step), no
+    transfer lowers a unit's cost: every finite entry is >= 0, and a 0
+    entry means a tie between the two centers' costs."""
+    J = small(1770, 400, 11, cm_max=6)
+    smin, _ = oracle.smin_order(J.cm)
+    tc, td = oracle.best_transfer(J.cm, smin)
+    fin = td >= 0
+    assert (tc[fin] >= 0).all() and (tc[fin] == 0).any()
+
+
 # ------------------------------------------------------- Bellman-Ford -----
 
 def _random_potential_graph(rng, N, density):
@@ -416,3 +487,38 @@ def test_road_cm_rejects_bad_graph():
     row_ptr2 = np.append(row_ptr, row_ptr[-1]).astype(np.int32)
     _, col2, w2 = _grid_csr(4, 4)
     assert oracle.road_cm(row_ptr2, col2, w2, [0], [16])[0] == oracle.ERR_ARG
+
+
+BT_MUTATIONS = {
+    "tie_takes_highest_unit": ("(t == tc[idx] && (int32_t)d < td[idx])",
+                               "(t == tc[idx] && (int32_t)d > td[idx])"),
+    "diagonal_kept": ("            if (v == u) continue;\n            int64_t t = (int64_t)cm[d * k + v]",
+                      "            int64_t t = (int64_t)cm[d * k + v]"),
+    "row_of_destination": ("int64_t idx = (int64_t)u * k + v;", "int64_t idx = v * k + u;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(BT_MUTATIONS))
+def test_planted_best_transfer_mistake_is_caught(name, tmp_path):
+    """Mistakes planted in a copy of the oracle's best-transfer table fail
+    the certificate of Defs. 8-10."""
+    old, new = BT_MUTATIONS[name]
+    src = open(_SRC).read()
+    assert src.count(old) == 1, name
+    mutated = tmp_path / "mut.c"
+    mutated.write_text(src.replace(old, new))
+    so = tmp_path / "mut.so"
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", str(mutated), "-o", str(so)],
+                   check=True)
+    lib = ctypes.CDLL(str(so))
+    P, i64 = ctypes.c_void_p, ctypes.c_int64
+    lib.oracle_best_transfer.argtypes = [i64, i64, P, P, P, P]
+    J = small(1780, 150, 7, cm_max=4)
+    assign = np.argmin(J.cm, axis=1).astype(np.int32)
+    cm = np.ascontiguousarray(J.cm, np.int32)
+    tc = np.empty((J.k, J.k), np.int64)
+    td = np.empty((J.k, J.k), np.int32)
+    assert lib.oracle_best_transfer(J.n, J.k, cm.ctypes.data, assign.ctypes.data,
+                                    tc.ctypes.data, td.ctypes.data) == 0
+    with pytest.raises(AssertionError):
+        _best_transfer_certificate(J.cm, assign, tc, td)
