@@ -376,7 +376,8 @@ int lbdd_best_transfer_noalloc(int32_t n, int32_t k, const void* cm_dev, int cm_
  * waits for it.  Scratch (k x V labels and per-CTA frontier queues) is
  * allocated from the stream-ordered pool and freed before returning.
  * Errors: LBDD_ERR_ARG (bad graph or ids, lengths that could overflow, a
- * demand node no center reaches), LBDD_ERR_CUDA, LBDD_ERR_OOM. */
+ * demand node no center reaches, a demand node that is a center's node:
+ * CM entries must be >= 1), LBDD_ERR_CUDA, LBDD_ERR_OOM. */
 int lbdd_road_cm(int32_t V, const int32_t* row_ptr, const int32_t* col, const int32_t* w,
                  int32_t k, const int32_t* centers, int32_t n, const int32_t* demand,
                  int32_t* cm, int64_t ld, void* stream);
