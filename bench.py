@@ -508,7 +508,8 @@ def run_batch(args):
                                "k log-uniform [10, 400), one CUDA-graph replay per step",
                    "instances": m, "total_rounds": rounds,
                    "plan_groups_C_clusters_instances": plan,
-                   "plan": "default cluster sizes, clusters per group by makespan search",
+                   "plan": "default cluster sizes; SMs shared between groups in proportion to "
+                           "their estimated SM-time",
                    "l2": "CMs total > L2 (1 GB)"},
         "rounds_per_s": rounds * args.steps / (ms / 1000.0),
         "sequential": {"value": seq_value, "unit": "solves/s", "instances_timed": len(seq_idx),

@@ -93,7 +93,8 @@ typedef struct lbdd_stats {
 
 /* Options for lbdd_set_option. */
 typedef enum lbdd_option {
-  LBDD_OPT_CLUSTER = 1,     /* CTAs per cluster for lbdd_solve, 1..16 (0 = auto) */
+  LBDD_OPT_CLUSTER = 1,     /* CTAs per cluster for lbdd_solve: 1, 2, 4, 8 or 16
+                               (0 = auto) */
   LBDD_OPT_NCYC_SKIP = 2,   /* 1 (default): skip Alg. 1's Bellman-Ford when the new
                                unit lowers no best-transfer cost (exact by Lemma 1);
                                0: always run it */

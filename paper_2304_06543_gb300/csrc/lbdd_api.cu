@@ -254,7 +254,7 @@ static int create_impl(lbdd_solver** out, int32_t n, int32_t k, const void* cm, 
   rc = ingest_cm(s, cm, cm_dtype, cm_is_device, cm_ld);
   if (rc) { free_all(s); delete s; return rc; }
   if (launch_smem(k, 16, s->elem) > kMaxSmem) { free_all(s); delete s; return LBDD_ERR_ARG; }
-  const int32_t max_pages = (n + kPage - 1) / kPage;
+  const int32_t max_pages = (int32_t)(((int64_t)n + kPage - 1) / kPage);
   const int32_t npages = max_pages + k;
   if (!rc) rc = dalloc(s, &s->cap, k);
   if (!rc) rc = dalloc(s, &s->pen, k);
@@ -439,7 +439,8 @@ extern "C" int lbdd_set_option(lbdd_solver* s, int option, int64_t value) {
   if (!s) return LBDD_ERR_ARG;
   switch (option) {
     case LBDD_OPT_CLUSTER:
-      if (value < 0 || value > 16) return LBDD_ERR_ARG;
+      // powers of two: the sizes the batch plans use and the tests cover
+      if (value < 0 || value > 16 || (value & (value - 1)) != 0) return LBDD_ERR_ARG;
       if (value > 0 && !fits(s, (int)value)) return LBDD_ERR_ARG;
       s->cluster = (int)value;
       return LBDD_OK;
