@@ -154,6 +154,26 @@ def _dptr(x) -> int:
     raise TypeError(type(x))
 
 
+def _host_vec(a, length: int, what: str) -> np.ndarray:
+    """Contiguous int32 host copy of a length-`length` vector (the C side reads
+    exactly that many entries)."""
+    v = np.ascontiguousarray(a, dtype=np.int32)
+    if v.shape != (length,):
+        raise ValueError(f"{what}: expected {length} entries, got shape {v.shape}")
+    return v
+
+
+def _numel(x) -> int:
+    return int(x.numel()) if hasattr(x, "numel") else int(np.asarray(x).size)
+
+
+def _need(x, count: int, what: str):
+    """A device tensor argument holds at least `count` elements (raw ints are
+    taken as they are)."""
+    if not isinstance(x, int) and _numel(x) < count:
+        raise ValueError(f"{what}: needs at least {count} elements, has {_numel(x)}")
+
+
 def _stream_handle(stream) -> int:
     if stream is None:
         try:
@@ -199,15 +219,18 @@ class Stats:
 def create(n, k, cm, cap, pen, stream=None, cm_dtype=None):
     """lbdd_create.  cm: numpy (n, k) int32/int16 (host) or a CUDA tensor."""
     lib = load()
-    cap = np.ascontiguousarray(cap, dtype=np.int32)
-    pen = np.ascontiguousarray(pen, dtype=np.int32)
+    cap = _host_vec(cap, int(k), "cap")
+    pen = _host_vec(pen, int(k), "pen")
     if isinstance(cm, np.ndarray):
         cm = np.ascontiguousarray(cm)
+        if cm.size != int(n) * int(k):
+            raise ValueError(f"cm: expected {n} x {k} entries, got shape {cm.shape}")
         dt = {np.dtype(np.int32): CM_I32, np.dtype(np.int16): CM_I16}[cm.dtype]
         ptr, is_dev = cm.ctypes.data, 0
     else:
         import torch
         dt = {torch.int32: CM_I32, torch.int16: CM_I16}[cm.dtype] if cm_dtype is None else cm_dtype
+        _need(cm, int(n) * int(k), "cm")
         ptr, is_dev = _dptr(cm), 1
     h = ctypes.c_void_p()
     _check(lib.lbdd_create(ctypes.byref(h), int(n), int(k), ptr, dt, is_dev, cap.ctypes.data,
@@ -218,8 +241,10 @@ def create(n, k, cm, cap, pen, stream=None, cm_dtype=None):
 def create_strict(n, k, cm, cap, stream=None):
     """lbdd_create_strict (Alg. 5).  cm: numpy (n, k) int32/int16 (host)."""
     lib = load()
-    cap = np.ascontiguousarray(cap, dtype=np.int32)
+    cap = _host_vec(cap, int(k), "cap")
     cm = np.ascontiguousarray(cm)
+    if cm.size != int(n) * int(k):
+        raise ValueError(f"cm: expected {n} x {k} entries, got shape {cm.shape}")
     dt = {np.dtype(np.int32): CM_I32, np.dtype(np.int16): CM_I16}[cm.dtype]
     h = ctypes.c_void_p()
     _check(lib.lbdd_create_strict(ctypes.byref(h), int(n), int(k), cm.ctypes.data, dt, 0,
@@ -230,16 +255,22 @@ def create_strict(n, k, cm, cap, stream=None):
 def road_cm(row_ptr, col, w, centers, demand, out, ld=None, stream=None):
     """lbdd_road_cm on device tensors (int32); out: device int32 (n, ld)."""
     n, k = len(demand), len(centers)
+    ld = int(ld if ld is not None else k)
+    if len(col) != len(w):
+        raise ValueError("col and w must have one entry per road")
+    _need(out, n * ld, "out")
     _check(load().lbdd_road_cm(int(len(row_ptr) - 1), _dptr(row_ptr), _dptr(col), _dptr(w),
                                int(k), _dptr(centers), int(n), _dptr(demand), _dptr(out),
-                               int(ld if ld is not None else k), _stream_handle(stream)),
+                               ld, _stream_handle(stream)),
            "lbdd_road_cm")
     return out
 
 
-def set_penalty_table(h, qtab):
+def set_penalty_table(h, qtab, k: int = None):
     """lbdd_set_penalty_table: qtab (k, Q) int32, q_s(j) = qtab[s, min(j, Q) - 1]."""
     q = np.ascontiguousarray(qtab, dtype=np.int32)
+    if q.ndim != 2 or q.shape[1] < 1 or (k is not None and q.shape[0] != k):
+        raise ValueError(f"qtab: expected a (k, Q) table, got shape {q.shape}")
     _check(load().lbdd_set_penalty_table(h, q.ctypes.data, int(q.shape[1])),
            "lbdd_set_penalty_table")
 
@@ -281,6 +312,7 @@ def assignment(h, n: int, out=None):
         a = np.empty(n, np.int32)
         _check(load().lbdd_assignment(h, a.ctypes.data, 0), "lbdd_assignment")
         return a
+    _need(out, n, "out")
     _check(load().lbdd_assignment(h, _dptr(out), 1), "lbdd_assignment")
     return out
 
@@ -330,6 +362,13 @@ def best_transfer_workspace(n: int, k: int) -> int:
 def best_transfer(n, k, cm_dev, cm_dtype, ld, assign_dev, tc_dev, td_dev, workspace,
                   workspace_bytes, stream=None):
     """lbdd_best_transfer (asynchronous on `stream`)."""
+    _need(cm_dev, int(n) * int(ld), "cm")
+    _need(assign_dev, int(n), "assign")
+    _need(tc_dev, int(k) * int(k), "tc")
+    _need(td_dev, int(k) * int(k), "td")
+    if not isinstance(workspace, int) and \
+            _numel(workspace) * workspace.element_size() < int(workspace_bytes):
+        raise ValueError(f"workspace: smaller than workspace_bytes = {workspace_bytes}")
     _check(load().lbdd_best_transfer(int(n), int(k), _dptr(cm_dev), int(cm_dtype), int(ld),
                                      _dptr(assign_dev), _dptr(tc_dev), _dptr(td_dev),
                                      _dptr(workspace), int(workspace_bytes),
@@ -368,7 +407,7 @@ class Solver:
         if phase_timers:
             set_option(self.h, OPT_PHASE_TIMERS, 1)
         if qtab is not None:
-            set_penalty_table(self.h, qtab)
+            set_penalty_table(self.h, qtab, self.k)
 
     def solve(self, max_rounds: int = -1):
         solve(self.h, max_rounds)
@@ -522,9 +561,11 @@ class Server:
     def submit(self, cm: np.ndarray, cap, pen) -> int:
         cm = np.ascontiguousarray(cm)
         dt = {np.dtype(np.int32): CM_I32, np.dtype(np.int16): CM_I16}[cm.dtype]
+        if cm.ndim != 2:
+            raise ValueError(f"cm: expected an (n, k) matrix, got shape {cm.shape}")
         n, k = cm.shape
-        cap = np.ascontiguousarray(cap, dtype=np.int32)
-        pen = np.ascontiguousarray(pen, dtype=np.int32)
+        cap = _host_vec(cap, k, "cap")
+        pen = _host_vec(pen, k, "pen")
         out = np.empty(n, np.int32)
         t = ctypes.c_int64()
         _check(load().lbdd_server_submit(self.h, int(n), int(k), cm.ctypes.data, dt,

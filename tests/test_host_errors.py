@@ -200,3 +200,22 @@ def test_binding_raises_without_a_gpu(lb):
         lb.Server(1 << 30)
     with pytest.raises(lb.LbddError):
         lb.tune_get(lb.CM_I32, 20, 1)
+
+
+def test_binding_checks_buffer_sizes(lb):
+    """The C side reads exactly n*k costs and k capacities and penalties: the
+    binding refuses arrays of other sizes before calling it."""
+    cm = np.ones((4, 3), np.int32)
+    ones3 = np.ones(3, np.int32)
+    with pytest.raises(ValueError):
+        lb.create(4, 3, cm, ones3[:2], ones3)
+    with pytest.raises(ValueError):
+        lb.create(4, 3, cm, ones3, np.ones(4, np.int32))
+    with pytest.raises(ValueError):
+        lb.create(5, 3, cm, ones3, ones3)
+    with pytest.raises(ValueError):
+        lb.create_strict(5, 3, cm, ones3)
+    with pytest.raises(ValueError):
+        lb.set_penalty_table(None, np.ones((3, 2), np.int32), k=4)
+    with pytest.raises(ValueError):
+        lb.set_penalty_table(None, np.ones(3, np.int32))
