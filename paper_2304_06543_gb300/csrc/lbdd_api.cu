@@ -241,6 +241,7 @@ static int create_impl(lbdd_solver** out, int32_t n, int32_t k, const void* cm, 
   *out = nullptr;
   if (n < 1 || k < 1 || !cm || !cap || !pen) return LBDD_ERR_ARG;
   if (k > 65535) return LBDD_ERR_ARG;   // Bellman-Ford packs node ids in 16 bits
+  if (k > lbdd_max_centers()) return LBDD_ERR_ARG;   // the cluster's shared memory
   if (cm_dtype != LBDD_CM_I32 && cm_dtype != LBDD_CM_I16) return LBDD_ERR_ARG;
   for (int32_t i = 0; i < k; ++i)
     if (cap[i] < 1 || pen[i] < 1) return LBDD_ERR_ARG;
@@ -330,6 +331,7 @@ extern "C" int lbdd_create_strict(lbdd_solver** out, int32_t n, int32_t k, const
     capsum += cap[i];
   }
   const int32_t K = capsum < n ? k + 1 : k;
+  if (K > lbdd_max_centers()) return LBDD_ERR_ARG;   // with the dummy center, if any
   int dev = 0, sms = 0;
   int rc = check_device(&dev, &sms);
   if (rc) return rc;

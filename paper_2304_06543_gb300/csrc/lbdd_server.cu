@@ -293,7 +293,8 @@ extern "C" int lbdd_server_create(lbdd_server** out, const lbdd_server_config* c
 extern "C" int lbdd_server_submit(lbdd_server* S, int32_t n, int32_t k, const void* cm,
                                   int cm_dtype, const int32_t* cap, const int32_t* pen,
                                   int32_t* assign_out, int64_t* ticket) {
-  if (!S || !ticket || n < 1 || k < 1 || k > 65535 || !cm || !cap || !pen || !assign_out)
+  if (!S || !ticket || n < 1 || k < 1 || k > lbdd_max_centers() || !cm || !cap || !pen ||
+      !assign_out)
     return LBDD_ERR_ARG;
   if (cm_dtype != LBDD_CM_I32 && cm_dtype != LBDD_CM_I16) return LBDD_ERR_ARG;
   for (int32_t i = 0; i < k; ++i)

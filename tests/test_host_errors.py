@@ -57,6 +57,13 @@ def test_create_rejects_bad_arguments(lb, lib):
     assert create(n=0) == lb.ERR_ARG
     assert create(k=0) == lb.ERR_ARG
     assert create(k=65536) == lb.ERR_ARG           # node ids are packed in 16 bits
+    kmax = lib.lbdd_max_centers()
+    wide = np.ones((2, kmax + 1), np.int32)
+    ones = np.ones(kmax + 1, np.int32)
+    h.value = None
+    assert lib.lbdd_create(ctypes.byref(h), 2, kmax + 1, _ptr(wide), lb.CM_I32, 0, _ptr(ones),
+                           _ptr(ones), None) == lb.ERR_ARG   # before any device work
+    assert h.value is None
     assert create(dtype=7) == lb.ERR_ARG
     assert create(cm=None) == lb.ERR_ARG
     assert create(cap=None) == lb.ERR_ARG
@@ -86,6 +93,12 @@ def test_create_strict_rejects_bad_arguments(lb, lib):
     c[0] = 0
     assert lib.lbdd_create_strict(ctypes.byref(h), n, k, _ptr(cm), lb.CM_I32, 0, _ptr(c),
                                   None) == lb.ERR_ARG
+    # k = the limit, capacities short of n: the dummy center makes k + 1
+    kmax = lib.lbdd_max_centers()
+    wide = np.ones((kmax + 1, kmax), np.int32)
+    ones = np.ones(kmax, np.int32)
+    assert lib.lbdd_create_strict(ctypes.byref(h), kmax + 1, kmax, _ptr(wide), lb.CM_I32, 0,
+                                  _ptr(ones), None) == lb.ERR_ARG
     assert h.value is None
 
 
