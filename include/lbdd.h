@@ -118,7 +118,7 @@ typedef enum lbdd_option {
  *                 int16 (exact, half the bytes per scan).
  *   cap, pen    : k entries each, host memory, cap[s] >= 1, pen[s] >= 1.
  *   cuda_stream : cudaStream_t for all work of this solver, or NULL.
- * On success *out owns device memory of about n*k*elem + 24*n + 8*k*k bytes.
+ * On success *out owns device memory of about n*k*elem + 32*n + 8*k*k bytes.
  * Errors: LBDD_ERR_ARG, LBDD_ERR_OOM, LBDD_ERR_CUDA, LBDD_ERR_NODEV; *out
  * is set to NULL on failure. */
 int lbdd_create(lbdd_solver** out, int32_t n, int32_t k, const void* cm, int cm_dtype,
