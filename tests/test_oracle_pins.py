@@ -479,6 +479,47 @@ def test_road_cm_equals_scipy_dijkstra():
     assert np.array_equal(cm, D[:, g.demand].T.astype(np.int64))
 
 
+def _csr_min(a, b, wts, V):
+    """Directed CSR of the roads a -> b; of parallel roads the shortest is kept."""
+    best = {}
+    for u, v, c in zip(a.tolist(), b.tolist(), wts.tolist()):
+        best[(u, v)] = min(best.get((u, v), c), c)
+    keys = sorted(best)
+    row_ptr = np.zeros(V + 1, np.int32)
+    np.add.at(row_ptr, np.array([u for u, _ in keys]) + 1, 1)
+    return (np.cumsum(row_ptr).astype(np.int32), np.array([v for _, v in keys], np.int32),
+            np.array([best[x] for x in keys], np.int32))
+
+
+def test_road_cm_one_way_roads_follow_the_direction():
+    """Directed roads: CM[d][s] is the length of the shortest path from
+    center s to demand node d (scipy Dijkstra from the centers), in the
+    graph as given and with every road reversed."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import dijkstra
+    rng = np.random.default_rng(7)
+    V = 300
+    src = np.concatenate([np.arange(V), rng.integers(0, V, 4 * V)])
+    dst = np.concatenate([(np.arange(V) + 1) % V, rng.integers(0, V, 4 * V)])   # a ring: connected
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    wts = rng.integers(1, 50, len(src))
+    centers = np.array([3, 77, 150, 299], np.int32)
+    demand = np.setdiff1d(np.arange(V), centers).astype(np.int32)
+    cms = []
+    for a, b in ((src, dst), (dst, src)):
+        row_ptr, col, w = _csr_min(a, b, wts, V)
+        rc, cm = oracle.road_cm(row_ptr, col, w, centers, demand)
+        assert rc == 0
+        D = dijkstra(csr_matrix((w.astype(np.float64), col, row_ptr), shape=(V, V)),
+                     directed=True, indices=centers)
+        assert np.array_equal(cm, D[:, demand].T.astype(np.int64))
+        cms.append(cm)
+    assert not np.array_equal(cms[0], cms[1])           # one-way roads: direction matters
+    # a demand node on a center's node would cost 0: refused (CM >= 1)
+    assert oracle.road_cm(row_ptr, col, w, centers, np.array([3], np.int32))[0] == oracle.ERR_ARG
+
+
 def test_road_cm_rejects_bad_graph():
     row_ptr, col, w = _grid_csr(4, 4)
     w[3] = 0
