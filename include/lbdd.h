@@ -188,9 +188,11 @@ int lbdd_reset(lbdd_solver* s);
  *     round, least first; instances that would outlast the rest of the
  *     batch move to faster clusters); without measurements about k/128
  *     CTAs; cluster_size > 0 forces one size for all;
- *   - instances with the same cost width and C form a group: one persistent
- *     launch whose clusters take instances from a device-side queue, the
- *     longest estimated solve first; the SMs are shared between the groups
+ *   - instances with the same cost width, C and solver options (strict,
+ *     lbdd_option flags) form a group, at most 16 groups per batch (more:
+ *     LBDD_ERR_ARG): one persistent launch whose clusters take instances
+ *     from a device-side queue, the longest estimated solve first; the SMs
+ *     are shared between the groups
  *     in proportion to their estimated SM-time (max_clusters > 0 caps each
  *     group's clusters) and the groups run concurrently;
  *   - one pass (set the round targets, the concurrent group launches, read
