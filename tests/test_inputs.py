@@ -88,3 +88,28 @@ def test_batch_sizes_log_uniform():
     # log-uniform: roughly half below the geometric midpoint
     assert 0.35 < np.mean(np.array(ns) < 10000) < 0.65
     assert 0.35 < np.mean(np.array(ks) < 63) < 0.65
+
+
+def test_road_network_structure():
+    """Two-way roads (the CSR holds both directions with equal lengths),
+    lengths >= 1, a connected grid, k distinct centers and every other node
+    one unit of demand; the same seed gives the same network."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+    g = L.road_network(5, 20, 13, 9)
+    assert g.V == 260 and len(g.row_ptr) == g.V + 1 and g.row_ptr[0] == 0
+    assert (np.diff(g.row_ptr) >= 2).all() and (g.w >= 1).all()
+    A = csr_matrix((g.w, g.col, g.row_ptr), shape=(g.V, g.V))
+    assert (A != A.T).nnz == 0
+    assert connected_components(A, directed=False)[0] == 1
+    assert len(np.unique(g.centers)) == 9
+    assert np.array_equal(np.sort(np.concatenate([g.centers, g.demand])), np.arange(g.V))
+    h = L.road_network(5, 20, 13, 9)
+    assert np.array_equal(g.w, h.w) and np.array_equal(g.centers, h.centers)
+
+
+def test_penalty_table_is_positive_and_non_decreasing():
+    q = L.penalty_table(3, 50, 12, base=(1, 40), step=(0, 15))
+    assert q.shape == (50, 12) and (q >= 1).all() and (np.diff(q, axis=1) >= 0).all()
+    assert (q[:, 0] <= 40).all() and (np.diff(q, axis=1) <= 15).all()
+    assert np.array_equal(q, L.penalty_table(3, 50, 12, base=(1, 40), step=(0, 15)))
