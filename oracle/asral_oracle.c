@@ -15,7 +15,7 @@
  * repeats); Q = 1 is the constant per-unit form of the experiments
  * (Section 5), where pen[s] is the table.
  *
- * Readings where the paper is silent or loose (all documented in DESIGN):
+ * Readings where the paper is silent or loose:
  *  - "ties are broken arbitrarily" (Defs. 9 and 10): the best-transfer edge
  *    u->v is the lexicographic minimum of (transfer cost, demand index);
  *  - "most suitable" center (Section 3.1): lowest index among the minima;
