@@ -244,6 +244,94 @@ def test_bellman_ford_matches_scipy_and_paths_are_tight():
                     assert dist[u] + W[u, v] == dist[v]
 
 
+def _canonical_parent_violations(bf, trials=80, seed=11):
+    """Count graphs where `bf`'s parent differs from the closed form: hop(v),
+    the sweep of v's last change, is the fewest edges among shortest paths to
+    v (levels of a breadth-first search over the tight edges
+    dist[u] + W[u][v] = dist[v], distances from scipy), and par[v] is the
+    lowest u with a tight edge and hop(u) = hop(v) - 1."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import bellman_ford
+    rng = np.random.default_rng(seed)
+    bad = 0
+    for t in range(trials):
+        N = int(rng.integers(3, 14))
+        W = _random_potential_graph(rng, N, [0.3, 0.6, 0.9][t % 3])
+        src = int(rng.integers(0, N))
+        rc, dist, par = bf(W, src)
+        if rc != 0:              # no negative cycle here: any error is a violation
+            bad += 1
+            continue
+        mask = W < oracle.INF
+        G = sp.csr_matrix((W[mask].astype(float), np.nonzero(mask)), shape=(N, N))
+        ref = bellman_ford(G, indices=src)
+        reach = ~np.isinf(ref)
+        d = np.where(reach, ref, 0).astype(np.int64)
+        tight = mask & reach[:, None] & reach[None, :] & \
+            (d[:, None] + np.where(mask, W, 0) == d[None, :])
+        hop = np.full(N, -1)
+        hop[src] = 0
+        level = [src]
+        while level:
+            nxt = []
+            for u in level:
+                for v in np.nonzero(tight[u])[0]:
+                    if hop[v] < 0:
+                        hop[v] = hop[u] + 1
+                        nxt.append(int(v))
+            level = nxt
+        for v in range(N):
+            if v != src and reach[v]:
+                cands = [u for u in range(N) if tight[u, v] and hop[u] == hop[v] - 1]
+                if par[v] != min(cands):
+                    bad += 1
+                    break
+    return bad
+
+
+def test_bellman_ford_parent_is_the_canonical_closed_form():
+    """Zero-cost edges of the random graphs make many ties."""
+    def bf(W, src):
+        rc, dist, par, _ = oracle.bellman_ford(W, src)
+        return rc, dist, par
+    assert _canonical_parent_violations(bf) == 0
+
+
+BF_MUTATIONS = {
+    "highest_predecessor_on_ties": ("if (c < best) { best = c; bu = (int32_t)u; }",
+                                    "if (c <= best) { best = c; bu = (int32_t)u; }"),
+    "update_on_equal_label": ("if (best < prev[v]) {", "if (best <= prev[v] && best < OR_INF) {"),
+    "in_place_sweep": ("int64_t c = prev[u] + w;", "int64_t c = (dist[u] < prev[u] ? dist[u] : prev[u]) + w;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(BF_MUTATIONS))
+def test_planted_bellman_ford_mistake_is_caught(name, tmp_path):
+    """Tie and sweep-order mistakes planted in a copy of the oracle's
+    Bellman-Ford break the canonical parents (or, updating on equal labels,
+    never converge)."""
+    old, new = BF_MUTATIONS[name]
+    src_text = open(_SRC).read()
+    assert src_text.count(old) == 1, name
+    mutated = tmp_path / "mut.c"
+    mutated.write_text(src_text.replace(old, new))
+    so = tmp_path / "mut.so"
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", str(mutated), "-o", str(so)],
+                   check=True)
+    lib = ctypes.CDLL(str(so))
+    P, i64 = ctypes.c_void_p, ctypes.c_int64
+    lib.oracle_bf.argtypes = [i64, i64, P, P, P, P]
+
+    def bf(W, src):
+        W = np.ascontiguousarray(W, np.int64)
+        N = W.shape[0]
+        dist = np.empty(N, np.int64)
+        par = np.empty(N, np.int32)
+        rc = lib.oracle_bf(N, src, W.ctypes.data, dist.ctypes.data, par.ctypes.data, None)
+        return rc, dist, par
+    assert _canonical_parent_violations(bf) > 0
+
+
 def test_bellman_ford_reports_negative_cycle():
     W = np.full((4, 4), oracle.INF, np.int64)
     W[0, 1], W[1, 2], W[2, 1], W[2, 3] = 1, -3, 1, 0
