@@ -63,3 +63,30 @@ def test_product_does_not_reference_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src
                 assert "asral_oracle" not in src and "_oracle.so" not in src
+
+
+def test_header_is_plain_c_and_a_c_program_links(tmp_path):
+    """include/lbdd.h is a C header (C11, pedantic, no warnings) and a C
+    program links against the library and calls it without any Python."""
+    import subprocess
+    import paper_2304_06543_gb300._build as b
+    src = tmp_path / "t.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "lbdd.h"\n'
+        "int main(void) {\n"
+        "  lbdd_solver* s = 0;\n"
+        "  int rc = lbdd_create(&s, 0, 5, 0, LBDD_CM_I32, 0, 0, 0, 0);\n"
+        '  printf("%d %lld %d\\n", rc, (long long)lbdd_cm_pitch(500, LBDD_CM_I16),\n'
+        "         (int)lbdd_max_centers());\n"
+        "  return rc == LBDD_ERR_ARG && s == 0 ? 0 : 1;\n}\n")
+    exe = tmp_path / "t"
+    libdir = os.path.dirname(b.LIB)
+    out = subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                          "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir,
+                          "-l:" + os.path.basename(b.LIB), f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                         capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert run.returncode == 0, run.stdout + run.stderr
+    rc, pitch, kmax = run.stdout.split()
+    assert int(pitch) == 504 and int(kmax) > 0
