@@ -128,6 +128,9 @@ def test_batch_rejects_bad_arguments(gpu_lib):
             gpu_lib.Batch([s], cluster_size=3)
         with pytest.raises(gpu_lib.LbddError):
             gpu_lib.solve_batch([s], cluster_size=32)
+        for C in (3, 6, 17):             # single solves take the batch sizes too
+            with pytest.raises(gpu_lib.LbddError):
+                gpu_lib.set_option(s.h, gpu_lib.OPT_CLUSTER, C)
 
 
 def test_full_batched_mix_matches_oracle_golden(gpu_lib):

@@ -74,6 +74,17 @@ def test_request_over_budget_fails_cleanly(gpu_lib):
         assert info.state == gpu_lib.REQ_FAILED and info.status == gpu_lib.ERR_BUDGET
 
 
+def test_submit_refuses_too_many_centers(gpu_lib):
+    k = gpu_lib.max_centers() + 1
+    cm = np.ones((2, k), np.int32)
+    ones = np.ones(k, np.int32)
+    with gpu_lib.Server(budget_bytes=1 << 30) as srv:
+        with pytest.raises(gpu_lib.LbddError) as e:
+            srv.submit(cm, ones, ones)
+        assert e.value.code == gpu_lib.ERR_ARG
+        assert srv.stats().queued == 0
+
+
 def test_destroy_with_work_outstanding(gpu_lib, reqs):
     insts, _ = reqs
     srv = gpu_lib.Server(budget_bytes=8 << 30, max_active=4, quantum_us=500)
