@@ -191,23 +191,46 @@ def make_instance(name):
     return lbdd_inputs.make_named(name, dtype="i16")
 
 
-def cpu_baseline(inst, rounds: int):
+def recorded_full_solve(name: str, inst):
+    """The oracle's whole-solve time stored with the workload's golden result
+    (written once by tests/golden/make_golden.py on the build host), if any."""
+    p = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("n") != inst.n or d.get("rounds") != inst.n or not d.get("oracle_seconds"):
+        return None
+    return {"seconds": d["oracle_seconds"], "solves_per_s": 1.0 / d["oracle_seconds"],
+            "source": f"tests/golden/{name}_oracle.json (one whole oracle solve, heap mode, "
+                      "one core of the x86 build host; not timed in this run)"}
+
+
+def cpu_baseline(inst, rounds: int, name: str = None):
     """The CPU oracle as it stands, single-threaded, on the first `rounds`
     rounds of the same instance; solves/s extrapolated linearly from the
-    prefix (optimistic for the oracle: later rounds are slower)."""
+    prefix (optimistic for the oracle: later rounds are slower).  The stored
+    whole-solve time of the workload, where one exists, rides along as
+    context."""
     import oracle
     cm32 = inst.cm.astype(np.int32)
+    done = min(rounds, inst.n)
     t0 = time.perf_counter()
-    res = oracle.asral(cm32, inst.cap, inst.pen, mode=oracle.MODE_HEAP, max_rounds=rounds)
+    res = oracle.asral(cm32, inst.cap, inst.pen, mode=oracle.MODE_HEAP, max_rounds=done)
     dt = time.perf_counter() - t0
     assert res.rc == 0
-    rps = rounds / dt
-    whole = rounds >= inst.n
-    return {"value": rps / inst.n, "unit": "solves/s" if whole else "solves/s (extrapolated)",
-            "cores": 1, "kind": "oracle",
-            "sample": f"first {rounds} of {inst.n} rounds, heap mode, {dt:.1f} s; "
-                      f"{rps:.1f} rounds/s",
-            "rounds_per_s": rps, "seconds": dt}
+    rps = done / dt
+    whole = done >= inst.n
+    out = {"value": rps / inst.n, "unit": "solves/s" if whole else "solves/s (extrapolated)",
+           "cores": 1, "kind": "oracle",
+           "sample": f"first {done} of {inst.n} rounds, heap mode, {dt:.1f} s; "
+                     f"{rps:.1f} rounds/s",
+           "rounds_per_s": rps, "seconds": dt}
+    rec = recorded_full_solve(name, inst) if name else None
+    if rec and not whole:
+        out["full_solve_recorded"] = rec
+    return out
 
 
 def run_reference(args):
@@ -394,7 +417,7 @@ def run_ours(args):
                "steps": args.e2e_steps}
 
     scan = None if args.no_scan else scan_roofline(lb, inst, hbm_peak, peak_kind, args.workload)
-    cpu = None if (args.no_cpu or rank != 0) else cpu_baseline(inst, args.cpu_rounds)
+    cpu = None if (args.no_cpu or rank != 0) else cpu_baseline(inst, args.cpu_rounds, args.workload)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,

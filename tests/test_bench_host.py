@@ -85,3 +85,13 @@ def test_traffic_entry_follows_its_sources():
         assert (got is not None) == current
         assert bench.committed_traffic(name, e["workload"] + "-other") is None
     assert bench.committed_traffic("no_such_kernel") is None
+
+
+def test_recorded_full_solve_time_comes_from_the_golden():
+    from types import SimpleNamespace
+    rec = bench.recorded_full_solve("city", SimpleNamespace(n=200_000))
+    with open(os.path.join(ROOT, "tests", "golden", "city_oracle.json")) as f:
+        gold = json.load(f)
+    assert rec["seconds"] == gold["oracle_seconds"] and rec["seconds"] > 1000
+    assert bench.recorded_full_solve("city", SimpleNamespace(n=1000)) is None   # other size
+    assert bench.recorded_full_solve("no_such_workload", SimpleNamespace(n=5)) is None
