@@ -90,3 +90,18 @@ def test_header_is_plain_c_and_a_c_program_links(tmp_path):
     assert run.returncode == 0, run.stdout + run.stderr
     rc, pitch, kmax = run.stdout.split()
     assert int(pitch) == 504 and int(kmax) > 0
+
+
+def test_every_exported_c_symbol_is_declared():
+    """No undocumented entry points: the library's exported lbdd_* C symbols
+    are exactly the functions include/lbdd.h declares."""
+    import shutil
+    import subprocess
+    import paper_2304_06543_gb300._build as b
+    if shutil.which("nm") is None:
+        pytest.skip("nm not available")
+    out = subprocess.run(["nm", "-D", "--defined-only", b.LIB], capture_output=True, text=True,
+                         check=True).stdout
+    exported = sorted({ln.split()[-1] for ln in out.splitlines()
+                       if ln.split() and ln.split()[-1].startswith("lbdd_")})
+    assert exported == declared_functions()
