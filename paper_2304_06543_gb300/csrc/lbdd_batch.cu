@@ -572,7 +572,11 @@ extern "C" int lbdd_tune_get(int cm_dtype, int32_t k, int cluster_size, double* 
     return LBDD_ERR_ARG;
   if (cm_dtype != LBDD_CM_I16 && cm_dtype != LBDD_CM_I32) return LBDD_ERR_ARG;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev >= kMaxDevices) return LBDD_ERR_NODEV;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();     // reported as LBDD_ERR_NODEV; leave no stale error
+    return LBDD_ERR_NODEV;
+  }
+  if (dev >= kMaxDevices) return LBDD_ERR_NODEV;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   *ns_per_round = g_tune[dev].ns[cm_dtype == LBDD_CM_I16 ? 0 : 1][bucket_of(k)][cidx(cluster_size)];
   return LBDD_OK;
