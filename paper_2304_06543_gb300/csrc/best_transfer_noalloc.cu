@@ -20,6 +20,7 @@ int bt_max_k(int elem_bytes);
 cudaError_t best_transfer_run(int32_t n, int32_t k, const void* cm, int elem_bytes, int64_t ld,
                               const int32_t* assign, int32_t* tc, int32_t* td, void* ws,
                               cudaStream_t st, int num_sms);
+int cuda_fail(cudaError_t e, const char* what);
 }  // namespace lbdd
 
 namespace {
@@ -40,11 +41,13 @@ int setup_device(int dev, void** addr, int* sms) {
   std::lock_guard<std::mutex> lk(g_setup_mu);
   if (!g_scratch_addr[dev]) {
     cudaDeviceProp prop;
-    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return LBDD_ERR_CUDA;
+    cudaError_t e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) return lbdd::cuda_fail(e, "cudaGetDeviceProperties");
     if (prop.major != 10 || prop.minor != 3) return LBDD_ERR_NODEV;
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_bt_scratch) != cudaSuccess || p == nullptr)
-      return LBDD_ERR_CUDA;
+    e = cudaGetSymbolAddress(&p, g_bt_scratch);
+    if (e != cudaSuccess) return lbdd::cuda_fail(e, "cudaGetSymbolAddress");
+    if (p == nullptr) return LBDD_ERR_CUDA;
     g_num_sms[dev] = prop.multiProcessorCount;
     g_scratch_addr[dev] = p;
   }
@@ -67,7 +70,9 @@ extern "C" int lbdd_best_transfer_noalloc(int32_t n, int32_t k, const void* cm_d
   // the scratch the scan needs must fit in the fixed array
   if (lbdd::bt_workspace_bytes(n, k) > kStaticScratchBytes) return LBDD_ERR_BUDGET;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBDD_ERR_CUDA;
+  const cudaError_t ed = cudaGetDevice(&dev);
+  if (ed != cudaSuccess) return lbdd::cuda_fail(ed, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return LBDD_ERR_CUDA;
   void* scratch = nullptr;
   int sms = 0;
   const int rc = setup_device(dev, &scratch, &sms);
@@ -77,5 +82,5 @@ extern "C" int lbdd_best_transfer_noalloc(int32_t n, int32_t k, const void* cm_d
   // so nothing left by an earlier call can leak into this one.
   const cudaError_t e = lbdd::best_transfer_run(n, k, cm_dev, elem, ld, assign_dev, tc_dev, td_dev,
                                                 scratch, static_cast<cudaStream_t>(stream), sms);
-  return e == cudaSuccess ? LBDD_OK : LBDD_ERR_CUDA;
+  return e == cudaSuccess ? LBDD_OK : lbdd::cuda_fail(e, "lbdd_best_transfer_noalloc");
 }
