@@ -352,7 +352,7 @@ int lbdd_best_transfer(int32_t n, int32_t k, const void* cm_dev, int cm_dtype, i
  *   caller's device buffers), without the workspace.
  *   Limit: lbdd_best_transfer_workspace(n, k) must not exceed 64 MiB, else
  *   LBDD_ERR_BUDGET is returned and nothing is launched (the city-scale
- *   200,000 x 500 case needs about 5 MiB).
+ *   200,000 x 500 case needs 6,072,320 bytes, about 5.8 MiB).
  *   The first call on each device looks up the device address of the array
  *   (with that device current); make that first call before any stream
  *   capture.

@@ -125,7 +125,8 @@ class Instance:
 
 # Workloads.  "tiny" is the small single instance (2,000 x 20); "city" the
 # city-scale single solve (200,000 x 500, clustered demand, road factors,
-# Zipf capacities); "large" the HBM-bound solve (2,000,000 x 2,000).
+# Zipf capacities); "large" the HBM-bound solve (2,000,000 x 2,000); "wide"
+# a test instance with the large one's k and tight capacity.
 CONFIGS = {
     "tiny": Recipe(n=2000, k=20, seed=1, layout="uniform", scale=100.0, cap_frac=0.9,
                    cap_dist="uniform", pen=(50, 500), name="tiny"),
@@ -133,6 +134,11 @@ CONFIGS = {
                    cap_frac=0.8, cap_dist="zipf", zipf=1.2, pen=(200, 2000), name="city"),
     "large": Recipe(n=2_000_000, k=2000, seed=3, layout="gmm", scale=1000.0, road=(1.0, 1.5),
                     cap_frac=0.85, cap_dist="zipf", zipf=1.2, pen=(100, 5000), name="large"),
+    # as "large" but with 20,000 units and total capacity 0.3 n: a solver
+    # whose k x k table does not fit a cluster's shared memory applies
+    # refinements from the first few hundred rounds on
+    "wide": Recipe(n=20_000, k=2000, seed=7, layout="gmm", scale=1000.0, road=(1.0, 1.5),
+                   cap_frac=0.3, cap_dist="uniform", pen=(100, 5000), name="wide"),
 }
 
 BATCH_SEED0 = 1000      # batched mix: instance i uses seed 1000 + i

@@ -386,7 +386,7 @@ class Solver:
 
     def __init__(self, cm, cap, pen, stream=None, cluster: int = 0, ncyc_skip: bool = True,
                  npath_reuse: bool = True, phase_timers: bool = False, strict: bool = False,
-                 qtab=None):
+                 qtab=None, tc_smem: bool = True):
         if isinstance(cm, np.ndarray):
             n, k = cm.shape
         else:
@@ -406,6 +406,8 @@ class Solver:
             set_option(self.h, OPT_NPATH_REUSE, 0)
         if phase_timers:
             set_option(self.h, OPT_PHASE_TIMERS, 1)
+        if not tc_smem:
+            set_option(self.h, OPT_TC_SMEM, 0)
         if qtab is not None:
             set_penalty_table(self.h, qtab, self.k)
 

@@ -7,7 +7,13 @@ and 2 are not reproducible from the text), so these files pin the oracle's
 own canonical results for regression and for GPU parity at sizes where
 re-running the oracle inside a test would take too long.
 
-Usage:  python tests/golden/make_golden.py tiny | city [rounds] | batch [count [procs]]
+Usage:  python tests/golden/make_golden.py tiny | city [rounds] | large|wide [rounds] [--table]
+        | batch [count [procs]]
+
+A prefix of the large or wide instance is written only if it applies at least one
+refinement (moves > 0), so that its parity test covers the applied paths;
+``--table`` also stores digests of the oracle's best-transfer table for the
+prefix's allotment.
 """
 from __future__ import annotations
 
@@ -32,13 +38,15 @@ def digest(a: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
 
 
-def run(name: str, rounds: int = -1) -> dict:
+def run(name: str, rounds: int = -1, table: bool = False) -> dict:
     inst = lbdd_inputs.make_named(name)
     t0 = time.time()
     res = oracle.asral(inst.cm, inst.cap, inst.pen, mode=oracle.MODE_HEAP, max_rounds=rounds)
     secs = time.time() - t0
     if res.rc != oracle.OK:
         raise SystemExit(f"oracle failed: {res.rc}")
+    if name in ("large", "wide") and rounds >= 0 and res.stats["moves"] == 0:
+        raise SystemExit(f"the first {rounds} rounds apply no refinement; take a longer prefix")
     out = {
         "workload": name,
         "n": inst.n,
@@ -54,6 +62,10 @@ def run(name: str, rounds: int = -1) -> dict:
         "oracle_mode": "heap",
         "source": "oracle.asral (CPU), written by tests/golden/make_golden.py",
     }
+    if table:
+        tc, td = oracle.best_transfer(inst.cm, res.assign)
+        out["table_tc_sha256"] = digest(np.where(tc >= oracle.INF, 2**31 - 1, tc).astype(np.int32))
+        out["table_td_sha256"] = digest(td.astype(np.int32))
     suffix = "" if rounds < 0 else f"_r{rounds}"
     path = os.path.join(HERE, f"{name}{suffix}_oracle.json")
     with open(path, "w") as f:
@@ -105,5 +117,7 @@ if __name__ == "__main__":
     if name == "batch":
         run_batch(int(args[1]) if len(args) > 1 else 256, int(args[2]) if len(args) > 2 else 4)
     else:
+        table = "--table" in args
+        args = [a for a in args if a != "--table"]
         rounds = int(args[1]) if len(args) > 1 else -1
-        run(name, rounds)
+        run(name, rounds, table)

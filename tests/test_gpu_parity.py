@@ -175,6 +175,13 @@ def test_city_prefix_matches_golden(gpu_lib):
                                                  rounds=3000)
     assert delta == gold["delta"]
     assert sha(assign.astype(np.int32)) == gold["assign_sha256"]
+    assert sha(loads.astype(np.int64)) == gold["load_sha256"]
+    assert st.moves == gold["stats"]["moves"] > 0
+    # the allotment is the oracle's (digest above), so the oracle's table of
+    # it (Defs. 8-10, by definition) is the expected incremental table
+    rtc, rtd = oracle.best_transfer(inst.cm, assign)
+    assert np.array_equal(tc, np.where(rtc >= oracle.INF, 2**31 - 1, rtc))
+    assert np.array_equal(td, rtd)
 
 
 def test_rejects_bad_input(gpu_lib):

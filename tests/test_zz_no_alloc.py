@@ -24,12 +24,13 @@ def _noalloc_fn(lib):
     return f
 
 
-def _device_cm(lb, inst):
+def _device_cm(lb, inst, cm_dtype):
     import torch
-    ld = lb.cm_pitch(inst.k, lb.CM_I16)
-    buf = torch.zeros(inst.n * ld + 128, dtype=torch.int16, device="cuda")
-    host = np.zeros((inst.n, ld), np.int16)
-    host[:, :inst.k] = inst.cm.astype(np.int16)
+    np_dt, t_dt = (np.int16, torch.int16) if cm_dtype == lb.CM_I16 else (np.int32, torch.int32)
+    ld = lb.cm_pitch(inst.k, cm_dtype)
+    buf = torch.zeros(inst.n * ld + 128, dtype=t_dt, device="cuda")
+    host = np.zeros((inst.n, ld), np_dt)
+    host[:, :inst.k] = inst.cm.astype(np_dt)
     buf[: inst.n * ld].copy_(torch.from_numpy(host.reshape(-1)))
     return buf, ld
 
@@ -38,12 +39,14 @@ def test_noalloc_matches_workspace_entry_point_twice(gpu_lib):
     import torch
     lib = gpu_lib.load()
     noalloc = _noalloc_fn(lib)
-    # two calls in a row on different instances: the second must not see
-    # anything the first left in the shared scratch
-    cases = [L.random_small(9100, n=30000, k=130, cm_max=400),
-             L.random_small(9101, n=7000, k=37, cm_max=9)]
-    for inst in cases:
-        buf, ld = _device_cm(gpu_lib, inst)
+    # calls in a row on different instances: each must not see anything the
+    # one before it left in the shared scratch; the last has int32 costs
+    # (the int32 scan reads up to 128 entries past the last row)
+    cases = [(L.random_small(9100, n=30000, k=130, cm_max=400), gpu_lib.CM_I16),
+             (L.random_small(9101, n=7000, k=37, cm_max=9), gpu_lib.CM_I16),
+             (L.random_small(9102, n=5000, k=61, cm_max=100000), gpu_lib.CM_I32)]
+    for inst, cm_dtype in cases:
+        buf, ld = _device_cm(gpu_lib, inst, cm_dtype)
         smin, _ = oracle.smin_order(inst.cm)
         assign = smin.copy()
         assign[::5] = -1
@@ -53,11 +56,11 @@ def test_noalloc_matches_workspace_entry_point_twice(gpu_lib):
         td_ref = torch.empty_like(tc_ref)
         wsb = gpu_lib.best_transfer_workspace(inst.n, k)
         ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
-        gpu_lib.best_transfer(inst.n, k, buf, gpu_lib.CM_I16, ld, a, tc_ref, td_ref, ws, wsb)
+        gpu_lib.best_transfer(inst.n, k, buf, cm_dtype, ld, a, tc_ref, td_ref, ws, wsb)
         tc = torch.full((k * k,), 7, dtype=torch.int32, device="cuda")
         td = torch.full((k * k,), 7, dtype=torch.int32, device="cuda")
         stream = torch.cuda.current_stream().cuda_stream
-        rc = noalloc(inst.n, k, buf.data_ptr(), gpu_lib.CM_I16, ld, a.data_ptr(), tc.data_ptr(),
+        rc = noalloc(inst.n, k, buf.data_ptr(), cm_dtype, ld, a.data_ptr(), tc.data_ptr(),
                      td.data_ptr(), stream)
         assert rc == 0, gpu_lib.strerror(rc)
         torch.cuda.synchronize()
