@@ -42,7 +42,8 @@ typedef enum lbdd_status {
   LBDD_ERR_ARG = -1,        /* invalid argument (sizes, CM < 1, cap < 1, pen < 1) */
   LBDD_ERR_OOM = -2,        /* device or host allocation failed */
   LBDD_ERR_CUDA = -3,       /* a CUDA runtime call failed */
-  LBDD_ERR_TIMEOUT = -4,    /* a bounded wait gave up (server polling) */
+  LBDD_ERR_TIMEOUT = -4,    /* a bounded wait gave up (server polling, or a solver
+                               kernel whose cluster exchange stopped answering) */
   LBDD_ERR_INVARIANT = -5,  /* Lemma 1/2 violated: Bellman-Ford did not converge */
   LBDD_ERR_STATE = -6,      /* call not valid in the object's current state */
   LBDD_ERR_NODEV = -7,      /* no CUDA device of compute capability 10.3 */

@@ -17,15 +17,18 @@
 //    shared memory when it fits (int16 when CM is int16), so Bellman-Ford
 //    relaxations read shared memory; the unit half stays in global memory;
 //  * Bellman-Ford is the synchronous form with a frontier (only labels that
-//    changed in the previous sweep can improve a label); each sweep publishes
-//    the owned label changes in shared memory and the CTAs read each other's
-//    changes through distributed shared memory after one cluster barrier;
+//    changed in the previous sweep can improve a label); after each sweep
+//    every CTA pushes a fixed-size message with its owned label changes into
+//    every other CTA's shared memory (st.async) and waits on a transaction
+//    barrier of its own for the messages of all others, so a sweep costs one
+//    one-way transfer instead of a cluster barrier plus a remote read;
 //  * when a unit changes center, the rows of T of the centers on the path are
 //    recomputed from their member lists (segment rescan), reading CM rows with
 //    16-byte vector loads.
 // Tie-breaking is canonical and identical to the CPU oracle: (cost, unit)
 // lexicographic in T, lowest predecessor index on equal Bellman-Ford labels.
 #include <limits>
+#include <type_traits>
 #include <mutex>
 
 #include "lbdd_device.cuh"
@@ -33,8 +36,8 @@
 namespace lbdd {
 
 struct Layout {
-  uint32_t dist, hop, load, cap, pen, front, par, outbox, npart, path, pathu, misc, red, tsm,
-      base_total, total;
+  uint32_t dist, hop, slack, pen, par, inbox, npart, path, pathu, misc, tail, rsink, elist, red, tsm,
+      msg, base_total, total;
 };
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -52,7 +55,14 @@ __host__ __device__ inline int32_t slice_stride(int32_t w, int32_t elem) {
 }
 
 constexpr uint32_t kRedBytes = kThreads * 8 * 8;  // rescan partials, int16 CM
-constexpr uint32_t kOutboxExtra = 4;              // outbox slots after the w key slots
+
+// Bytes of one CTA's Bellman-Ford message for one sweep: a label per owned
+// column (4 bytes with int16 costs, 8 with int32 costs), then a 16-byte tail
+// (merge flag, padding, sink key).  A multiple of 16 because w is a
+// multiple of 16 / elem.
+__host__ __device__ inline uint32_t msg_bytes(int32_t w, int32_t elem) {
+  return (uint32_t)w * (elem == 2 ? 4u : 8u) + 16u;
+}
 
 // Shared-memory carve-up; `base_total` excludes the cost slice, `total`
 // includes it (k x w entries of elem bytes).
@@ -62,32 +72,41 @@ __host__ __device__ inline Layout make_layout(int32_t k, int32_t C, int32_t elem
   const int32_t vpl = 16 / elem;
   const uint32_t w = (uint32_t)own_width(k, C, vpl);
   const uint32_t ku = (uint32_t)k, Cu = (uint32_t)C;
-  L.dist = o;   o = align16(o + 8u * ku);
-  L.hop = o;    o = align16(o + 4u * ku);
-  L.load = o;   o = align16(o + 4u * ku);
-  L.cap = o;    o = align16(o + 4u * ku);
+  L.msg = msg_bytes((int32_t)w, elem);
+  L.dist = o;   o = align16(o + 8u * w);                // labels of the owned columns
+  L.hop = o;    o = align16(o + 4u * w);
+  L.slack = o;  o = align16(o + 4u * ku);               // load - capacity per center
   L.pen = o;    o = align16(o + 4u * ku);
-  L.front = o;  o = align16(o + 8u * (ku + 1));       // frontier keys of the current sweep
   L.par = o;    o = align16(o + 4u * w);
-  L.outbox = o; o = align16(o + 2u * (w + kOutboxExtra) * 8u);   // [2][w + extra] published keys
-  L.npart = o;  o = align16(o + Cu * 16u);             // per-CTA partial minima
+  L.inbox = o;  o = align16(o + 2u * Cu * L.msg);       // [2][C] messages, by sweep parity
+  L.npart = o;  o = align16(o + Cu * 16u);               // per-CTA partial minima
   L.path = o;   o = align16(o + 4u * (ku + 2));
   L.pathu = o;  o = align16(o + 4u * (ku + 2));
   L.misc = o;   o = align16(o + 8u * 16u);
-  L.red = o;    o = align16(o + kRedBytes);
+  L.tail = o;   o = align16(o + 8u * kMaxCluster);      // count and merge flag per sender
+  L.rsink = o;  o = align16(o + 8u * kWarps);           // per-warp NPath sink candidates
+  L.elist = o;  o = align16(o + (elem == 2 ? 8u : 16u) * 32u * kWarps);   // per-warp frontier lists
+  // rescan partials, and the per-warp column minima of a sweep ([kWarps][w + 1] keys)
+  const uint32_t redb = 8u * kWarps * (w + 1);
+  L.red = o;    o = align16(o + (redb > kRedBytes ? redb : kRedBytes));
   L.base_total = o;
   L.tsm = o;    o = align16(o + (uint32_t)elem * ku * (uint32_t)slice_stride((int32_t)w, elem));
   L.total = o;
   return L;
 }
 
-// Outbox of one sweep: w key slots, then these (index w + OB_*).
-enum { OB_MERGE = 0, OB_SINK, OB_SLOTS };
-constexpr uint64_t kNoKey = ~0ull;   // empty slot (no real key has all bits set)
-static_assert(OB_SLOTS <= (int)kOutboxExtra, "outbox extra slots");
+constexpr uint64_t kNoKey = ~0ull;   // no candidate (no real key has all bits set)
 // Slots of the per-CTA scalar block.
-enum { MS_SINK_DIST = 0, MS_SINK_PAR, MS_LCNT0, MS_LCNT1, MS_PATHLEN, MS_SINK_KEY, MS_NAFF,
-       MS_MERGE_ANY, MS_STOP0, MS_STOP1 };
+enum { MS_SINK_DIST = 0, MS_SINK_PAR, MS_PATHLEN, MS_NAFF, MS_MERGE_ANY, MS_STOP0, MS_STOP1,
+       MS_ABORT, MS_SINK_IN };
+
+// Longest wait for the other CTAs' messages of one sweep (globaltimer ns).
+// A sweep's messages arrive within microseconds; reaching this limit means
+// a broken exchange, which is reported as LBDD_ERR_TIMEOUT.
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+// Longest sleep inside one barrier test (the waiting warp wakes when the
+// phase completes, so a long limit only keeps the warp from spinning).
+constexpr uint32_t kSleepNs = 10000000;
 
 // Rounds between two checks of the launch's time quantum.
 constexpr int kQuantumCheck = 8;
@@ -109,6 +128,13 @@ struct Solver {
   static constexpr int VPL = 16 / (int)sizeof(T);
   using TS = T;                                           // cost type of the shared slice
   static constexpr int32_t kTsInf = std::numeric_limits<TS>::max();
+  // Bellman-Ford label of a frontier node and in a message.  With int16
+  // costs every transfer edge is below 2^15 in magnitude and a frontier
+  // label sums at most k + 1 <= 4801 of them, so 32 bits hold it exactly
+  // (the sink, whose penalty edges are larger, is never a frontier node and
+  // travels as a 64-bit key).  int32 costs need 64 bits.
+  using LT = typename std::conditional<sizeof(T) == 2, int32_t, int64_t>::type;
+  static constexpr LT kNoLab = std::numeric_limits<LT>::max();
 
   const DevInst& I;   // shared-memory copy of the current instance
   const T* cm;
@@ -117,14 +143,18 @@ struct Solver {
   int flags;
   bool quantum_on;    // the launch is time-sliced (Book::deadline set)
   bool tsm_on;        // owned cost slice resident in shared memory
-  int64_t* s_dist;    // labels of the owned columns (and 0 at the source)
-  int32_t* s_hop;     // sweep of each owned column's last label change
-  int32_t* s_load;
-  int32_t* s_cap;     // capacity replica
+  int64_t* s_dist;    // [w] labels of the owned columns
+  int32_t* s_hop;     // [w] sweep of each owned column's last label change
+  int32_t* s_slack;   // [k] load - capacity of every center (>= 0: no vacancy)
   int32_t* s_pen;     // [k] penalty one more unit would pay at each center, q_c(load_c - cap_c + 1)
-  uint64_t* s_front;  // frontier keys ((label + 2^47) << 16 | node) of the current sweep
   int32_t* s_par;     // parents of the owned columns
-  uint64_t* s_outbox; // [2][w + OB_SLOTS]: keys ((label + 2^47) << 16 | node) published per sweep
+  unsigned char* s_inbox;  // [2][C] messages of every CTA, by sweep parity (msg_bytes each)
+  uint32_t mbytes;    // bytes of one message
+  uint64_t* s_mbar;   // [2][kMaxCluster] transaction barriers, by parity and sender
+  uint32_t mph;       // phase parity of the barriers of each message parity
+  int32_t* s_tail;    // [kMaxCluster][2] count and merge flag of each sender's last message
+  uint64_t* s_rsink;  // [kWarps] per-warp NPath sink candidates
+  unsigned char* s_elist;  // [kWarps][32] per-warp frontier entries (label, node)
   int64_t* s_npart;   // [C][2]: per-CTA partial minima (label; hop << 16 | node)
   int32_t* s_path;
   int32_t* s_pathu;
@@ -258,7 +288,7 @@ struct Solver {
     const T* r = row(d);
     int32_t bv = INT32_MAX, bj = -1;
     for (int s = tid; s < k; s += kThreads) {
-      if (s_load[s] < s_cap[s]) {
+      if (s_slack[s] < 0) {
         const int32_t v = (int32_t)r[s];
         if (v < bv) { bv = v; bj = s; }
       }
@@ -448,13 +478,10 @@ struct Solver {
   }
 
   // -------------------------------------------------------- Bellman-Ford --
-  // Lexicographic minimum of (label[u] + weight(u, v), u) over this
-  // lane's share of the frontier (entries g, g+G, ...).
-  // A frontier entry packs (label, node) so that one unsigned 64-bit minimum
-  // is the lexicographic minimum of (label, node): node in the low 16 bits
-  // (k <= 65535), label + 2^47 above it (labels are sums of at most k+1 edge
-  // weights below 2^31 in magnitude, so |label| < 2^47).  Adding an edge
-  // weight t shifted by 16 bits keeps the node bits intact.
+  // Keys pack (label, node) so that one unsigned 64-bit minimum is the
+  // lexicographic minimum of (label, node): node in the low 16 bits
+  // (k <= 65535), label + 2^47 above it (labels are sums of at most k + 1
+  // edge weights below 2^31 in magnitude, so |label| < 2^47).
   static __device__ __forceinline__ uint64_t pack_key(int64_t label, int32_t node) {
     return ((uint64_t)(label + ((int64_t)1 << 47)) << 16) | (uint32_t)node;
   }
@@ -462,61 +489,21 @@ struct Solver {
     return (int64_t)(key >> 16) - ((int64_t)1 << 47);
   }
 
-  // Minimum packed key of (label[u] + weight(u, v), u) over the frontier
-  // entries slice, slice+step, ...  Lanes of a warp hold consecutive owned
-  // columns and walk the same frontier entries, so the key read is a
-  // broadcast and the cost reads are consecutive (no bank conflicts).
-  template <bool STRICT>
-  __device__ __forceinline__ uint64_t relax_column(int cl, bool valid, int slice, int step,
-                                                   int nfront, int32_t j, bool npath,
-                                                   int32_t pen_j) const {
-    uint64_t best = ~0ull;
-    const int v = c0 + cl;
-    if (!valid) return best;
-    if (v == j && npath) {             // Def. 10 (c): q_u() - q_{s*}()
-      for (int f = slice; f < nfront; f += step) {
-        const uint64_t key = s_front[f];
-        const int32_t u = (int32_t)(key & 0xffffu);
-        if (u == j) continue;
-        const int64_t t = (int64_t)(s_load[u] >= s_cap[u] ? s_pen[u] : 0) - pen_j;
-        best = min(best, key + ((uint64_t)t << 16));
-      }
-      return best;
-    }
-    // transfer edges u -> v (v == j: into s*in)
-    constexpr int U = 4;
-    int f = slice;
-    if (tsm_on) {
-      const TS* col = s_tc + cl;
-      for (; f + (U - 1) * step < nfront; f += U * step) {
-        uint64_t key[U];
-        int32_t t[U];
-#pragma unroll
-        for (int q = 0; q < U; ++q) key[q] = s_front[f + q * step];
-#pragma unroll
-        for (int q = 0; q < U; ++q) t[q] = (int32_t)col[(int32_t)(key[q] & 0xffffu) * ws];
-#pragma unroll
-        for (int q = 0; q < U; ++q) {
-          if (STRICT) t[q] = strict_cost(t[q], (int32_t)(key[q] & 0xffffu), kTsInf);
-          if (t[q] != kTsInf) best = min(best, key[q] + ((uint64_t)(int64_t)t[q] << 16));
-        }
-      }
-      for (; f < nfront; f += step) {
-        const uint64_t key = s_front[f];
-        int32_t t = (int32_t)col[(int32_t)(key & 0xffffu) * ws];
-        if (STRICT) t = strict_cost(t, (int32_t)(key & 0xffffu), kTsInf);
-        if (t != kTsInf) best = min(best, key + ((uint64_t)(int64_t)t << 16));
-      }
-    } else {
-      const int32_t* col = I.tc + c0 + cl;
-      for (; f < nfront; f += step) {
-        const uint64_t key = s_front[f];
-        int32_t t = col[(int64_t)(key & 0xffffu) * k];
-        if (STRICT) t = strict_cost(t, (int32_t)(key & 0xffffu), kTInf);
-        if (t != kTInf) best = min(best, key + ((uint64_t)(int64_t)t << 16));
-      }
-    }
-    return best;
+  // Message of CTA r for the sweep of parity p, in this CTA's inbox.
+  __device__ __forceinline__ unsigned char* msg(int parity, int r) const {
+    return s_inbox + ((uint32_t)(parity * C + r)) * mbytes;
+  }
+  __device__ __forceinline__ LT* msg_lab(unsigned char* m) const { return reinterpret_cast<LT*>(m); }
+  // message tail: merge flag, padding, sink key
+  __device__ __forceinline__ int32_t* msg_merge(unsigned char* m) const {
+    return reinterpret_cast<int32_t*>(m + mbytes - 16);
+  }
+  __device__ __forceinline__ uint64_t* msg_sink(unsigned char* m) const {
+    return reinterpret_cast<uint64_t*>(m + mbytes - 8);
+  }
+  // Transaction barrier of this CTA for CTA r's messages of parity p.
+  __device__ __forceinline__ uint64_t* mbar(int parity, int r) const {
+    return s_mbar + parity * kMaxCluster + r;
   }
 
   // q_c(x), x >= 1: penalty of the x-th allotment beyond capacity (Def. 4).
@@ -527,38 +514,112 @@ struct Solver {
   // constant penalty (Q = 1) the replica never changes, so callers skip the
   // update (a global load on the round's critical path).
   __device__ __forceinline__ int32_t qnext(int32_t c) const {
-    return qval(c, s_load[c] - s_cap[c] + 1);
+    return qval(c, s_slack[c] + 1);
   }
   // q_j of the anchor's last unit beyond capacity (load > cap).
   __device__ __forceinline__ int32_t qlast(int32_t j) const {
-    return I.Q == 1 ? s_pen[j] : qval(j, s_load[j] - s_cap[j]);
+    return I.Q == 1 ? s_pen[j] : qval(j, s_slack[j]);
   }
 
   // Alg. 5 edge cost: a center with a vacancy can pass a dummy unit on for
   // free, so its transfer costs are min(T, 0) (an absent edge becomes 0).
   __device__ __forceinline__ int32_t strict_cost(int32_t t, int32_t u, int32_t inf) const {
-    return (t == inf || t > 0) && s_load[u] < s_cap[u] ? 0 : t;
+    return (t == inf || t > 0) && s_slack[u] < 0 ? 0 : t;
   }
 
-  // Strict improvement of owned column cl.  Returns the frontier key to
-  // publish for it (kNoKey if its label did not improve); the sink column
-  // (v == j) publishes its candidate in the outbox's sink slots instead and
-  // is never a frontier node.  Only the owner reads and writes the label of
-  // an owned column.
-  __device__ __forceinline__ uint64_t record(int cl, uint64_t best, int32_t j, int64_t sink_dist,
-                                             int sweep, uint64_t* ob) {
-    const int v = c0 + cl;
-    if (v == j) {   // the sink's (label, parent) in the key encoding
-      ob[w + OB_SINK] = best != ~0ull && key_label(best) < sink_dist ? best : kNoKey;
-      return kNoKey;
+  // Cost of the transfer edge u -> owned column cl; kTsInf (TSM: slice in
+  // shared memory) or kTInf (slice in global memory) for no edge.
+  template <bool TSM>
+  __device__ __forceinline__ int32_t edge(int32_t u, int cl) const {
+    if (TSM) return (int32_t)s_tc[u * ws + cl];
+    return I.tc[(int64_t)u * k + c0 + cl];
+  }
+
+  // One frontier entry of a warp's list: a label and its node.
+  struct Ent {
+    LT l;
+    int32_t u;
+  };
+
+  // Relaxes the edges out of the n entries el[0..n) (node order) into owned
+  // column cl (lane = column; `colok` false: no such column), folding the
+  // candidates into (bl, bu); the strict "<" keeps the lowest node among
+  // equal labels.  Warp-uniform n.
+  template <bool STRICT, bool TSM>
+  __device__ __forceinline__ void relax_list(const Ent* el, int n, int cl, bool colok, LT& bl,
+                                             int32_t& bu) const {
+    constexpr int32_t inf = TSM ? kTsInf : kTInf;
+    constexpr int U = 4;
+    int f = 0;
+    for (; f + U - 1 < n; f += U) {
+      Ent e[U];
+      int32_t t[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) e[q] = el[f + q];
+#pragma unroll
+      for (int q = 0; q < U; ++q) t[q] = colok ? edge<TSM>(e[q].u, cl) : inf;
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        if (STRICT) t[q] = strict_cost(t[q], e[q].u, inf);
+        const LT c = e[q].l + (LT)t[q];
+        if (t[q] != inf && c < bl) { bl = c; bu = e[q].u; }
+      }
     }
-    if (best == ~0ull) return kNoKey;
+    for (; f < n; ++f) {
+      const Ent e = el[f];
+      int32_t t = colok ? edge<TSM>(e.u, cl) : inf;
+      if (STRICT) t = strict_cost(t, e.u, inf);
+      const LT c = e.l + (LT)t;
+      if (t != inf && c < bl) { bl = c; bu = e.u; }
+    }
+  }
+
+  // Strict improvement of owned column cl < wr.  Returns the label to
+  // publish for it (kNoLab if it did not improve); the sink column (v == j)
+  // writes its candidate key into the message tail instead and is never a
+  // frontier node.  Only the owner reads and writes an owned column's label.
+  __device__ __forceinline__ LT record(int cl, uint64_t best, int32_t j, int64_t sink_dist,
+                                       int sweep, unsigned char* my) {
+    const int v = c0 + cl;
+    if (v == j) {
+      *msg_sink(my) = best != ~0ull && key_label(best) < sink_dist ? best : kNoKey;
+      return kNoLab;
+    }
+    if (best == ~0ull) return kNoLab;
     const int64_t bc = key_label(best);
-    if (bc >= s_dist[v]) return kNoKey;
-    s_dist[v] = bc;
-    s_hop[v] = sweep;
+    if (bc >= s_dist[cl]) return kNoLab;
+    s_dist[cl] = bc;
+    s_hop[cl] = sweep;
     s_par[cl] = (int32_t)(best & 0xffffu);
-    return pack_key(bc, v);
+    return (LT)bc;
+  }
+
+  // Frontier-size statistics (phase timers only): a sweep relaxing `n` labels.
+  __device__ __forceinline__ void front_stat(int n) {
+    B->front_sum += n;
+    B->front_hist[n <= 1 ? 0 : n <= 4 ? 1 : n <= 16 ? 2 : n <= 64 ? 3 : n <= 256 ? 4 : 5]++;
+  }
+
+  // Waits until the message of CTA r for the sweep of parity p is in: the
+  // calling warp sleeps on the barrier (lane 0 of the first such warp
+  // announces the message's bytes).  Bounded: past kWaitLimitNs the CTA
+  // records LBDD_ERR_TIMEOUT and goes on.
+  __device__ __forceinline__ void wait_message(int p, int r, bool announce) {
+    uint64_t* b = mbar(p, r);
+    if (announce && (tid & 31) == 0) mbar_arrive_expect(b, mbytes);
+    __syncwarp();
+    const uint32_t parity = (mph >> p) & 1u;
+    if (!mbar_try_wait(b, parity, kSleepNs)) {
+      const uint64_t t0 = gtimer_ns();
+      while (!mbar_try_wait(b, parity, kSleepNs)) {
+        if (gtimer_ns() - t0 > kWaitLimitNs) {
+          s_misc[MS_ABORT] = 1;   // read after the next CTA barrier
+          atomicExch(reinterpret_cast<unsigned long long*>(I.ctl + CTL_STATUS),
+                     (unsigned long long)(int64_t)ST_ERR_TIMEOUT);
+          break;
+        }
+      }
+    }
   }
 
   // Canonical synchronous Bellman-Ford from the anchor j (Alg. 3 / Sections
@@ -569,168 +630,198 @@ struct Solver {
   // No edge enters the source.  Labels change only on strict improvement and
   // take the lowest-index predecessor among equal candidates.
   //
-  // Exchange: every sweep each CTA writes one outbox slot per owned column
-  // (the improved label's key, or kNoKey) plus its merge flag and, at the
-  // owner of column j, the sink candidate.  After the sweep's cluster barrier
-  // every thread pulls one slot of one CTA through distributed shared memory
-  // and the valid keys are compacted (warp ballots) into the next frontier.
-  // A CTA changes at most w labels per sweep, so the outbox has a fixed size
-  // and needs no counts.  Outboxes are double-buffered by sweep parity: a
-  // buffer is rewritten two barriers after it was read.
+  // Sweep s: every CTA writes a message (the new label of each owned column
+  // that improved, kNoLab for the others, its merge flag and, at the owner
+  // of column j, the sink candidate) into its own inbox slot and
+  // bulk-copies it into the same slot of every other CTA's inbox (warp p to
+  // the p-th other CTA; the copy engine moves the data, so the load/store
+  // pipe stays free for relaxations), completing bytes on the receiver's
+  // barrier for that sender and parity.  Sweep s + 1 relaxes the edges out
+  // of the labels of sweep s (the frontier): the 16 warps are split among
+  // the C senders; each warp waits only for its sender's message, compacts
+  // its share of the sender's improved labels into a list of its own and
+  // relaxes them into every owned column (lane = column), so relaxation
+  // overlaps the arrival of the other messages.  A shared-memory transpose
+  // then combines the warps' per-column minima.  Every CTA sees the same
+  // messages, so all of them take the same decisions.  A CTA's slot r of a
+  // parity is rewritten by CTA r two sweeps later, after r received this
+  // CTA's next message, which this CTA sends after it has read the slot; and
+  // a CTA rewrites its own slot (the copies' source) only after every other
+  // CTA's next message arrived, each sent after the copy into it completed.
   // Returns 1 for a negative sink label (path to apply), 0 for none, and
-  // < 0 on a broken invariant.  `merged` says whether this CTA's merge of
-  // the round's unit lowered a cost of row j (NegCycle only).
+  // < 0 on a broken invariant (-1) or exchange (-2).  `merged` says whether
+  // this CTA's merge of the round's unit lowered a cost of row j (NegCycle
+  // only).
   __device__ int bellman_ford(int32_t j, bool npath, bool merged, bool allow_skip) {
     for (int cl = tid; cl < w; cl += kThreads) {
-      const int v = c0 + cl;
-      if (v < k) { s_dist[v] = (v == j) ? 0 : kDInf; s_hop[v] = (v == j) ? 0 : -1; }
+      s_dist[cl] = kDInf;
+      s_hop[cl] = -1;
       s_par[cl] = -1;
     }
-    if (tid == 0) {
-      s_dist[j] = 0;
-      s_hop[j] = 0;
-      s_front[0] = pack_key(0, j);
-      s_misc[MS_LCNT0] = 0;
-      s_misc[MS_LCNT1] = 0;
-    }
+    if (tid == 0) s_misc[MS_ABORT] = 0;
     __syncthreads();
     const int owner_j = j / w;
     // NPath (Def. 10 (c)): the penalty the anchor's last unit beyond capacity paid
     const int32_t pen_j = npath ? qlast(j) : 0;
-    const int obs = w + (int)kOutboxExtra;
     const bool strict = flags & OPT_STRICT;
-    // lanes own 32 consecutive columns (a column block); the WPB warps of a
-    // block split the frontier and their minima are combined in shared memory
-    const int CB = max(1, (wr + 31) / 32);
-    const int WPB = max(1, kWarps / CB);
+    const bool sink_here = npath && rank == owner_j;   // this CTA relaxes Def. 10 (c) edges
     const int lane = tid & 31, warp = tid >> 5;
-    uint64_t* red_k = reinterpret_cast<uint64_t*>(s_red + 256);           // [WPB][CB*32]
-    // every thread keeps the same copy of the sink label and the frontier
-    // size; they change only at cluster barriers
+    const int WPS = kWarps / C;                         // warps per sender
+    const int src = warp / WPS, sub = warp - src * WPS;
+    const int ncb = (w + 31) / 32;                      // column blocks
+    const int RS = w + 1;                               // row stride of the partial minima
+    uint64_t* red = reinterpret_cast<uint64_t*>(s_red);  // [kWarps][RS] per-warp column minima
+    Ent* el = reinterpret_cast<Ent*>(s_elist) + warp * 32;
+    uint32_t lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
     int64_t sink_dist = kDInf;
     int32_t sink_par = -1;
-    int nfront = 1;
     int result = 0;
     bool skipped_bf = false;
     for (int sweep = 1;; ++sweep) {
-      const uint64_t t0 = timer() ? clock_cycles() : 0;
-      const int pb = buf;                      // outbox written in this sweep
-      uint64_t* ob = s_outbox + pb * obs;
-      if (timer()) {
-        B->front_sum += nfront;
-        B->front_hist[nfront <= 1 ? 0 : nfront <= 4 ? 1 : nfront <= 16 ? 2 : nfront <= 64 ? 3
-                      : nfront <= 256 ? 4 : 5]++;
-      }
-      // relax all edges out of the frontier into the owned columns, then
-      // publish every owned column's slot
-      if (WPB > 1) {
-        const int blk = warp / WPB, slice = warp % WPB;
-        if (blk < CB) {
-          const int cl = blk * 32 + lane;
-          red_k[slice * CB * 32 + cl] =
-              strict ? relax_column<true>(cl, cl < wr, slice, WPB, nfront, j, npath, pen_j)
-                     : relax_column<false>(cl, cl < wr, slice, WPB, nfront, j, npath, pen_j);
-        }
-        __syncthreads();
-        if (timer()) B->t_rloop += clock_cycles() - t0;
-        for (int cl = tid; cl < w; cl += kThreads) {
-          uint64_t key = kNoKey;
-          if (cl < wr) {
-            uint64_t best = ~0ull;
-            for (int sl = 0; sl < WPB; ++sl) best = min(best, red_k[sl * CB * 32 + cl]);
-            key = record(cl, best, j, sink_dist, sweep, ob);
+      const bool tmr = timer();
+      const uint64_t t0 = tmr ? clock_cycles() : 0;
+      if (tmr && sweep == 1) front_stat(1);
+      const int pb = buf;        // parity of the message this sweep writes
+      const int q = pb ^ 1;      // parity of the messages it reads (sweep - 1)
+      // ---- relax the frontier (labels of sweep - 1; the source at sweep 1)
+      unsigned char* in = msg(q, src);
+      const LT* labs = msg_lab(in);
+      if (sweep > 1 && src != rank) wait_message(q, src, sub == 0);
+      uint64_t skey = ~0ull;     // this warp's best NPath sink candidate
+      int cnt = 0;               // improved labels of the sender (sub 0)
+      const int nsb = sweep > 1 ? (w + 31) / 32 : 1;
+      for (int cb = 0; cb < ncb; ++cb) {
+        const int cl = cb * 32 + lane;
+        const bool colok = cl < wr && !(sink_here && c0 + cl == j);
+        LT bl = kNoLab;
+        int32_t bu = -1;
+        for (int sb = 0; sb < nsb; ++sb) {
+          LT l = 0;
+          bool valid = lane == 0 && src == 0;   // sweep 1: the source alone
+          if (sweep > 1) {
+            const int s = sb * 32 + lane;
+            l = s < w ? labs[s] : kNoLab;
+            valid = l != kNoLab;
           }
-          ob[cl] = key;
+          unsigned bits = __ballot_sync(0xffffffffu, valid);
+          if (cb == 0) cnt += __popc(bits);
+          if (WPS > 1) {   // the sender's entries are shared among its warps
+            valid = valid && (int)(__popc(bits & lt) % WPS) == sub;
+            bits = __ballot_sync(0xffffffffu, valid);
+          }
+          const int32_t u = (sweep > 1 ? src * w + sb * 32 : j) + lane;
+          if (cb == 0 && sink_here) {   // Def. 10 (c): q_u() - q_{s*}()
+            uint64_t key = ~0ull;
+            if (valid && u != j) key = pack_key((int64_t)l + (s_slack[u] >= 0 ? s_pen[u] : 0) - pen_j, u);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+              key = min(key, (uint64_t)__shfl_xor_sync(0xffffffffu, key, off));
+            skey = min(skey, key);
+          }
+          const int n = __popc(bits);
+          if (n == 0) continue;
+          __syncwarp();   // earlier reads of the list are done
+          if (valid) el[__popc(bits & lt)] = Ent{l, u};
+          __syncwarp();
+          if (tsm_on) {
+            if (strict) relax_list<true, true>(el, n, cl, colok, bl, bu);
+            else relax_list<false, true>(el, n, cl, colok, bl, bu);
+          } else {
+            if (strict) relax_list<true, false>(el, n, cl, colok, bl, bu);
+            else relax_list<false, false>(el, n, cl, colok, bl, bu);
+          }
         }
-      } else {
-        for (int blk = warp; blk < CB; blk += kWarps) {
-          const int cl = blk * 32 + lane;
-          const uint64_t best =
-              strict ? relax_column<true>(cl, cl < wr, 0, 1, nfront, j, npath, pen_j)
-                     : relax_column<false>(cl, cl < wr, 0, 1, nfront, j, npath, pen_j);
-          if (cl < w) ob[cl] = cl < wr ? record(cl, best, j, sink_dist, sweep, ob) : kNoKey;
+        if (cl < w) red[warp * RS + cl] = bu < 0 ? ~0ull : pack_key(bl, bu);
+      }
+      if (lane == 0) s_rsink[warp] = skey;
+      if (sweep > 1 && sub == 0 && lane == 0) {   // the sender's tail, for the decisions
+        s_tail[2 * src] = cnt;
+        s_tail[2 * src + 1] = *msg_merge(in);
+        if (src == owner_j) s_misc[MS_SINK_IN] = (int64_t)*msg_sink(in);
+      }
+      if (tmr) B->t_rloop += clock_cycles() - t0;
+      __syncthreads();
+      const uint64_t t1 = tmr ? clock_cycles() : 0;
+      // ---- decisions on the messages of sweep - 1 (the same in every CTA)
+      if (sweep > 1) {
+        mph ^= 1u << q;
+        const int total = __reduce_add_sync(0xffffffffu, lane < C ? s_tail[2 * lane] : 0);
+        const bool any_merge =
+            __ballot_sync(0xffffffffu, lane < C && s_tail[2 * lane + 1] != 0) != 0u;
+        if (tmr) front_stat(total);
+        const uint64_t sink_key = (uint64_t)s_misc[MS_SINK_IN];
+        const bool sink_chg = sink_key != kNoKey;
+        if (sink_chg) {
+          sink_dist = key_label(sink_key);
+          sink_par = (int32_t)(sink_key & 0xffffu);
         }
-        for (int cl = CB * 32 + tid; cl < w; cl += kThreads) ob[cl] = kNoKey;
-        if (timer()) B->t_rloop += clock_cycles() - t0;
+        if (s_misc[MS_ABORT] != 0) { result = -2; break; }   // exchange timed out
+        if (sweep == 2 && allow_skip && !any_merge) {
+          // T is unchanged since the last round, whose Gamma had no negative
+          // cycle (Lemmas 1/2): the NegCycle sink label cannot be negative.
+          if (rank == 0 && tid == 0) B->skipped++;
+          result = 0;
+          skipped_bf = true;
+          break;
+        }
+        if (total == 0 && !sink_chg) {   // sweep - 1 changed nothing: converged
+          if (rank == 0 && tid == 0) {
+            B->bf_calls++;
+            B->bf_sweeps += sweep - 1;
+            B->bf_max = max(B->bf_max, (int64_t)(sweep - 1));
+          }
+          result = sink_dist < 0 ? 1 : 0;
+          break;
+        }
+        if (sweep - 1 >= k + 1) { result = -1; break; }
+      }
+      // ---- combine the warps' minima per owned column, record, write the message
+      unsigned char* my = msg(pb, rank);
+      LT* lab = msg_lab(my);
+      for (int base = 0; base < w; base += 2 * kWarps) {
+        const int cl = base + 2 * warp + (lane >> 4);
+        const int sw = lane & 15;
+        uint64_t best = ~0ull;
+        if (cl < w) best = sink_here && c0 + cl == j ? s_rsink[sw] : red[sw * RS + cl];
+#pragma unroll
+        for (int off = 8; off > 0; off >>= 1)
+          best = min(best, (uint64_t)__shfl_xor_sync(0xffffffffu, best, off));
+        if (sw == 0 && cl < w) lab[cl] = cl < wr ? record(cl, best, j, sink_dist, sweep, my) : kNoLab;
       }
       if (tid == 0) {
-        ob[w + OB_MERGE] = merged ? 1 : 0;
-        if (rank != owner_j) ob[w + OB_SINK] = kNoKey;
+        *msg_merge(my) = merged ? 1 : 0;
+        if (rank != owner_j) *msg_sink(my) = kNoKey;
+        s_misc[MS_SINK_IN] = (int64_t)kNoKey;
       }
-      if (timer()) B->t_rred += clock_cycles() - t0;
-      const uint64_t t1 = timer() ? clock_cycles() : 0;
-      cluster_sync_all();
-      const uint64_t t2 = timer() ? clock_cycles() : 0;
-      commit_pending();
-      // pull every CTA's outbox: one slot per thread, valid keys compacted
-      // into the next frontier (its order is irrelevant: relaxation takes a
-      // minimum); counter pb was zeroed after the previous barrier
-      int* cnt = reinterpret_cast<int*>(&s_misc[MS_LCNT0 + pb]);
-      if (tid == 0) s_misc[MS_LCNT0 + (pb ^ 1)] = 0;
-      const int nslots = C * w;
-      for (int base = warp * 32; base < nslots; base += kThreads) {
-        const int idx = base + lane;
-        uint64_t key = kNoKey;
-        if (idx < nslots) {
-          const int r = idx / w;
-          key = C == 1 ? s_outbox[pb * obs + idx]
-                       : (uint64_t)dsmem_ld64(dsmem_addr(s_outbox + pb * obs + (idx - r * w), (uint32_t)r));
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, key != kNoKey);
-        if (m != 0u) {
-          int at = 0;
-          if (lane == 0) at = atomicAdd(cnt, __popc(m));
-          at = __shfl_sync(0xffffffffu, at, 0);
-          if (key != kNoKey) s_front[at + __popc(m & ((1u << lane) - 1u))] = key;
-        }
+      __syncthreads();   // the message is complete
+      const uint64_t t2 = tmr ? clock_cycles() : 0;
+      if (C > 1 && warp < C - 1 && lane == 0) {   // warp p copies the message to the p-th other CTA
+        const uint32_t peer = (uint32_t)(warp < rank ? warp : warp + 1);
+        fence_proxy_async_smem();
+        bulk_copy_to_cta(dsmem_addr(my, peer), my, mbytes, dsmem_addr(mbar(pb, rank), peer));
       }
-      bool my_merge = false;
-      if (tid < C)
-        my_merge = dsmem_ld64(dsmem_addr(s_outbox + pb * obs + w + OB_MERGE, (uint32_t)tid)) != 0;
-      if (tid == kThreads - 32)
-        s_misc[MS_SINK_KEY] =
-            dsmem_ld64(dsmem_addr(s_outbox + pb * obs + w + OB_SINK, (uint32_t)owner_j));
-      const bool any_merge = __syncthreads_or(my_merge) != 0;
-      const int total = *cnt;
-      const uint64_t sink_key = (uint64_t)s_misc[MS_SINK_KEY];
-      const bool sink_chg = sink_key != kNoKey;
-      if (sink_chg) {
-        sink_dist = key_label(sink_key);
-        sink_par = (int32_t)(sink_key & 0xffffu);
-      }
-      nfront = total;
-      if (timer()) {
+      // the allotment of the round's unit enters the member lists off the
+      // sweep's critical path (every CTA finished reading them once the
+      // messages of sweep 1 were in)
+      if (sweep == 2) commit_pending();
+      if (tmr) {
         const uint64_t t3 = clock_cycles();
         B->t_relax += t1 - t0;
         B->t_sync += t2 - t1;
         B->t_gather += t3 - t2;
       }
       buf ^= 1;
-      if (sweep == 1 && allow_skip && !any_merge) {
-        // T is unchanged since the last round, whose Gamma had no negative
-        // cycle (Lemmas 1/2): the NegCycle sink label cannot be negative.
-        if (rank == 0 && tid == 0) B->skipped++;
-        result = 0;
-        skipped_bf = true;
-        break;
-      }
-      if (total == 0 && !sink_chg) {
-        if (rank == 0 && tid == 0) {
-          B->bf_calls++;
-          B->bf_sweeps += sweep;
-          B->bf_max = max(B->bf_max, (int64_t)sweep);
-        }
-        result = sink_dist < 0 ? 1 : 0;
-        break;
-      }
-      if (sweep >= k + 1) { result = -1; break; }
     }
+    commit_pending();   // if the call ended at its first decision
     if (tid == 0) {
       s_misc[MS_SINK_DIST] = sink_dist;
       s_misc[MS_SINK_PAR] = sink_par;
       s_misc[MS_MERGE_ANY] = skipped_bf ? 0 : 1;   // 1: the labels converged
     }
     __syncthreads();
+    // the path walk reads the owners' parent arrays: order their writes
+    if (result > 0 && C > 1) cluster_sync_all();
     return result;
   }
 
@@ -753,9 +844,9 @@ struct Solver {
     };
     for (int cl = tid; cl < wr; cl += kThreads) {
       const int u = c0 + cl;
-      if (u == j || s_dist[u] >= kDInf) continue;
-      const int64_t c = s_dist[u] + (int64_t)(s_load[u] >= s_cap[u] ? s_pen[u] : 0) - pen_j;
-      const uint32_t hu = ((uint32_t)s_hop[u] << 16) | (uint32_t)u;
+      if (u == j || s_dist[cl] >= kDInf) continue;
+      const int64_t c = s_dist[cl] + (int64_t)(s_slack[u] >= 0 ? s_pen[u] : 0) - pen_j;
+      const uint32_t hu = ((uint32_t)s_hop[cl] << 16) | (uint32_t)u;
       if (better(c, hu, bc, bhu)) { bc = c; bhu = hu; }
     }
     for (int off = 16; off > 0; off >>= 1) {
@@ -827,7 +918,7 @@ struct Solver {
         const int32_t to = (i + 1 < m) ? s_path[i + 1] : (npath ? -1 : j);
         int32_t x = to >= 0 ? __ldcg(I.td + (int64_t)from * k + to) : -1;
         // Alg. 5: a dummy unit moves where the edge cost came from a vacancy
-        const bool dummy = strict && to >= 0 && s_load[from] < s_cap[from] &&
+        const bool dummy = strict && to >= 0 && s_slack[from] < 0 &&
                            __ldcg(I.tc + (int64_t)from * k + to) > 0;
         if (dummy) x = -1;
         else if (to >= 0 && (uint32_t)x >= (uint32_t)n) { x = -1; if (rank == 0) B->err0 = ST_ERR_INVARIANT; }
@@ -886,8 +977,8 @@ struct Solver {
       }
     }
     if (npath && tid == 0) {   // load and penalty replicas in every CTA
-      s_load[j] -= 1;
-      s_load[s_path[m - 1]] += 1;
+      s_slack[j] -= 1;
+      s_slack[s_path[m - 1]] += 1;
       if (I.Q > 1) {
         s_pen[j] = qnext(j);
         s_pen[s_path[m - 1]] = qnext(s_path[m - 1]);
@@ -896,8 +987,8 @@ struct Solver {
     if ((flags & OPT_STRICT) && tid == 0) {
       for (int i = 0; i < m; ++i) {
         const int32_t x_out = s_pathu[i], x_in = s_pathu[i > 0 ? i - 1 : m - 1];
-        if (x_out >= 0 && x_in < 0) s_load[s_path[i]] -= 1;
-        else if (x_out < 0 && x_in >= 0) s_load[s_path[i]] += 1;
+        if (x_out >= 0 && x_in < 0) s_slack[s_path[i]] -= 1;
+        else if (x_out < 0 && x_in >= 0) s_slack[s_path[i]] += 1;
       }
     }
     __syncthreads();
@@ -992,9 +1083,8 @@ struct Solver {
     const int64_t r_begin = I.ctl[CTL_ROUNDS];
     const int64_t r_end = min((int64_t)n, I.ctl[CTL_TARGET]);
     for (int v = tid; v < k; v += kThreads) {
-      s_load[v] = __ldcg(I.load + v);
-      s_cap[v] = __ldg(I.cap + v);
-      s_pen[v] = qval(v, s_load[v] - s_cap[v] + 1);
+      s_slack[v] = __ldcg(I.load + v) - __ldg(I.cap + v);
+      s_pen[v] = qval(v, s_slack[v] + 1);
     }
     if (rank == 0 && tid == 0) {
       B->delta = I.ctl[CTL_DELTA];
@@ -1033,11 +1123,11 @@ struct Solver {
       const bool strict = flags & OPT_STRICT;
       const int32_t j = strict ? strict_target(d) : __ldcg(I.smin + d);
       if ((uint32_t)j >= (uint32_t)k) { status = ST_ERR_INVARIANT; break; }
-      const bool over = !strict && s_load[j] >= __ldg(I.cap + j);
+      const bool over = !strict && s_slack[j] >= 0;
       const int32_t q_over = over ? s_pen[j] : 0;   // q_j(load - cap + 1), Alg. 2
       const bool merged = merge_row(d, j);
       if (tid == 0) {
-        s_load[j] += 1;
+        s_slack[j] += 1;
         if (!strict && I.Q > 1) s_pen[j] = qnext(j);
       }
       if (rank == 0 && tid == 0) {
@@ -1052,7 +1142,7 @@ struct Solver {
       pending_d = d;
       pending_j = j;
       int res = bellman_ford(j, false, merged, allow_skip);
-      if (res < 0) { status = ST_ERR_INVARIANT; break; }
+      if (res < 0) { status = res == -2 ? ST_ERR_TIMEOUT : ST_ERR_INVARIANT; break; }
       // labels converged (not skipped) and nothing applied: Alg. 4 can reuse them
       const bool reusable = (s_misc[MS_MERGE_ANY] != 0 || !allow_skip) && res == 0;
       if (res > 0) {
@@ -1064,7 +1154,7 @@ struct Solver {
       if (over) {
         res = reusable && !(flags & OPT_NO_NPATH_REUSE) ? npath_from_ncyc(j)
                                                          : bellman_ford(j, true, true, false);
-        if (res < 0) { status = ST_ERR_INVARIANT; break; }
+        if (res < 0) { status = res == -2 ? ST_ERR_TIMEOUT : ST_ERR_INVARIANT; break; }
         if (res > 0) {
           const int m = walk_path(j);
           if (m < 2) { status = ST_ERR_INVARIANT; break; }
@@ -1127,6 +1217,7 @@ asral_cluster_kernel(const DevInst* __restrict__ insts, int ninst, int* work_cou
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ DevInst s_inst;
   __shared__ Book s_book;
+  __shared__ __align__(8) uint64_t s_mbar[2 * kMaxCluster];
   Solver<T> S(s_inst);
   S.B = &s_book;
   S.tid = threadIdx.x;
@@ -1134,6 +1225,10 @@ asral_cluster_kernel(const DevInst* __restrict__ insts, int ninst, int* work_cou
   S.C = (int)cluster_nrank();
   S.flags = flags;
   S.buf = 0;
+  S.s_mbar = s_mbar;
+  S.mph = 0;
+  if (S.tid < 2 * kMaxCluster) mbar_init(&s_mbar[S.tid], 1);
+  if (S.tid == 0) mbar_fence_init();   // the cluster barrier before the first instance publishes them
   S.quantum_on = quantum_ns != 0;
   if (S.rank == 0 && S.tid == 0) s_book.deadline = S.quantum_on ? gtimer_ns() + quantum_ns : 0;
   int64_t* s_item = reinterpret_cast<int64_t*>(smem);   // first 16 bytes: work item
@@ -1177,12 +1272,14 @@ asral_cluster_kernel(const DevInst* __restrict__ insts, int ninst, int* work_cou
     S.tsm_on = 16 + L.total <= avail && !(flags & OPT_NO_TC_SMEM);
     S.s_dist = reinterpret_cast<int64_t*>(base + L.dist);
     S.s_hop = reinterpret_cast<int32_t*>(base + L.hop);
-    S.s_load = reinterpret_cast<int32_t*>(base + L.load);
-    S.s_cap = reinterpret_cast<int32_t*>(base + L.cap);
+    S.s_slack = reinterpret_cast<int32_t*>(base + L.slack);
     S.s_pen = reinterpret_cast<int32_t*>(base + L.pen);
     S.s_par = reinterpret_cast<int32_t*>(base + L.par);
-    S.s_front = reinterpret_cast<uint64_t*>(base + L.front);
-    S.s_outbox = reinterpret_cast<uint64_t*>(base + L.outbox);
+    S.s_inbox = base + L.inbox;
+    S.mbytes = L.msg;
+    S.s_tail = reinterpret_cast<int32_t*>(base + L.tail);
+    S.s_rsink = reinterpret_cast<uint64_t*>(base + L.rsink);
+    S.s_elist = base + L.elist;
     S.s_npart = reinterpret_cast<int64_t*>(base + L.npart);
     S.s_path = reinterpret_cast<int32_t*>(base + L.path);
     S.s_pathu = reinterpret_cast<int32_t*>(base + L.pathu);

@@ -472,6 +472,7 @@ extern "C" int lbdd_set_option(lbdd_solver* s, int option, int64_t value) {
 int lbdd::status_to_rc(int64_t st) {
   if (st == 0) return LBDD_OK;
   if (st == ST_ERR_INVARIANT) return LBDD_ERR_INVARIANT;
+  if (st == ST_ERR_TIMEOUT) return LBDD_ERR_TIMEOUT;
   return LBDD_ERR_STATE;
 }
 

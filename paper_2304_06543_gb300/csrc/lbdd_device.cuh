@@ -58,6 +58,7 @@ enum CtlIndex {
 // Status codes shared with include/lbdd.h.
 enum : int64_t {
   ST_OK = 0,
+  ST_ERR_TIMEOUT = -4,     // a bounded wait inside a kernel ran out
   ST_ERR_INVARIANT = -5,
 };
 
@@ -152,6 +153,80 @@ __device__ __forceinline__ void dsmem_st32(uint32_t addr, int32_t v) {
 }
 __device__ __forceinline__ void dsmem_st64(uint32_t addr, int64_t v) {
   asm volatile("st.shared::cluster.s64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+
+// ------------------------------------------------- transaction barriers ---
+// A CTA's mbarrier in its own shared memory, completed by one local arrival
+// plus a byte count of asynchronous stores from the other CTAs of the
+// cluster (st.async ... mbarrier::complete_tx::bytes).  The stores may land
+// before the local arrival announces their byte count: the pending count
+// then goes negative, and the phase still completes only once the arrival
+// and all announced bytes are in.
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t arrivals) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(arrivals)
+               : "memory");
+}
+// Makes initialised barriers visible to the other CTAs of the cluster (a
+// cluster barrier must follow before any of them signals this barrier).
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// The local arrival of the current phase, announcing `bytes` of incoming
+// asynchronous stores.
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;"
+               ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// True once the phase of parity `parity` has completed; acquires the
+// asynchronous stores of the cluster that completed it.  The thread may
+// sleep inside the instruction for up to `sleep_ns` while the phase is open
+// (it wakes when the phase completes), so a waiting warp issues few
+// instructions.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity,
+                                              uint32_t sleep_ns = 0) {
+  uint32_t done;
+  if (sleep_ns == 0) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done) : "r"(smem_u32(bar)), "r"(parity), "r"(sleep_ns) : "memory");
+  }
+  return done != 0;
+}
+// Orders this thread's view of earlier generic-proxy writes to shared
+// memory (by any thread of the CTA, after a CTA barrier) before later
+// bulk copies that read it.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// from this CTA's shared memory into another CTA's shared memory (cluster
+// address `dst`), completing the bytes on that CTA's barrier at cluster
+// address `bar`.  The copy engine moves the data; the issuing thread does
+// not wait.
+__device__ __forceinline__ void bulk_copy_to_cta(uint32_t dst, const void* src, uint32_t bytes,
+                                                 uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(dst), "r"(smem_u32(src)), "r"(bytes), "r"(bar) : "memory");
+}
+// 16 bytes into another CTA's shared memory (cluster address `dst`),
+// completing that many bytes on its barrier at cluster address `bar`.
+__device__ __forceinline__ void st_async16(uint32_t dst, int4 v, uint32_t bar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"
+      ::"r"(dst), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(bar) : "memory");
 }
 
 // ------------------------------------------------------------ CM access ---
