@@ -111,7 +111,7 @@ typedef enum lbdd_option {
 
 /* Create a solver for one LBDD instance (Section 2.1 inputs).
  *   n, k        : demand units and service centers, n >= 1,
- *                 1 <= k <= lbdd_max_centers() (4,800; larger k returns
+ *                 1 <= k <= lbdd_max_centers() (5,376; larger k returns
  *                 LBDD_ERR_ARG).
  *   cm          : n*k entries, demand-major, every entry >= 1; dtype per
  *                 cm_dtype; host memory unless cm_is_device != 0.

