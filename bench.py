@@ -1,17 +1,24 @@
-"""Benchmark: complete ASRAL solves of the city-scale LBDD instance on GB300.
+"""Benchmark of the GB300 ASRAL library (arXiv 2304.06543) on synthetic LBDD workloads.
 
-One step = one full solve (Alg. 2: prologue + all n rounds, every Alg. 1 /
-Alg. 4 refinement) of the 200,000 x 500 city-scale instance (30-component
-Gaussian-mixture demand, road factors, Zipf capacities summing to 0.8 n,
-penalties in [200, 2000]), int16 cost matrix resident in HBM.  The metric is
-solves/s (higher is better).  Multi-GPU runs are independent replicas (the
-method has no data-parallel split of one solve): every rank solves its own
-copy, value = total solves / slowest rank's time.
+Default workload ("headline"): the serving stream.  Each step is `--per-step`
+requests of the stream (95% sized like the batched mix, n 1e3-1e5 and k
+10-400; 5% large, `--large`); the K steps arrive at once and are served by the
+request server (continuous batching: admission under a device-memory budget,
+time-sliced passes over all resident requests) from CMs resident in device
+memory.  value = requests / time (solves/s, higher is better).  The same
+requests are then served under Poisson arrivals (p50/p99 latency), from host
+memory (`e2e`), and one at a time (`sequential`, the served-over-sequential
+ratio); every served result equals the lone solve, and the small requests the
+CPU oracle solves equal the oracle's.  Sub-keys: `batched` (256 instances in
+one CUDA-graph replay vs one at a time, against the stored oracle results),
+`scan` (the full best-transfer table of the 2,000,000 x 2,000 instance, int16
+and int32, against measured HBM bandwidth), `city_solve` (one whole
+200,000 x 500 solve, the solver kernel's roofline), `cpu_baseline` (the oracle
+on one core).  Multi-GPU runs are replicas: each rank serves a round-robin
+share of the stream and of the batched mix (no data-path collective), and the
+value counts all ranks' requests over the slowest rank's time.
 
-Extra keys: `e2e` (the same solve through the C ABI from pinned host memory,
-copies included), `roofline` (the solver kernel against measured HBM
-bandwidth), `scan` (the standalone best-transfer scan, the HBM-bound kernel),
-`cpu_baseline` (the CPU oracle on a bounded prefix of the same instance).
+Other workloads (one measurement each): city, tiny, batch, serve, large, road.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -32,7 +39,7 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-METRIC = "solves/s"
+METRIC = "solves/s"          # the whole-solve workloads (city, tiny)
 WORKLOAD = "city-scale ASRAL solve: |D|=200,000 x |S|=500, CM int16 (400 MB int32 source)"
 TINY_WORKLOAD = "tiny ASRAL solve: |D|=2,000 x |S|=20 uniform points, CM int16"
 
@@ -42,14 +49,18 @@ def solve_workload_label(name: str) -> str:
     return WORKLOAD if name == "city" else TINY_WORKLOAD
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["city", "tiny", "batch", "serve", "large", "road"],
-                    default="city")
+    ap.add_argument("--workload", choices=["headline", "city", "tiny", "batch", "serve", "large",
+                                           "road"], default="headline")
+    ap.add_argument("--per-step", type=int, default=4,
+                    help="headline: serving-stream requests per step")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0,
+                    help="headline: seconds of CPU oracle solves for cpu_baseline")
     ap.add_argument("--large-rounds", type=int, default=20000,
                     help="large: solver rounds timed on the 2,000,000 x 2,000 instance")
     ap.add_argument("--batch-size", type=int, default=256, help="batch: instances in the mix")
@@ -57,18 +68,18 @@ def parse():
                     help="batch: time one-at-a-time solves of every m-th instance (1 = all)")
     ap.add_argument("--requests", type=int, default=64, help="serve: requests in the stream")
     ap.add_argument("--large", default="100000x1000",
-                    help="serve: size n x k of the large requests (5%% of the stream)")
-    ap.add_argument("--quantum-us", type=int, default=20000, help="serve: pass length")
-    ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: device memory budget")
+                    help="headline/serve: size n x k of the large requests (5%% of the stream)")
+    ap.add_argument("--quantum-us", type=int, default=20000, help="serving: pass length")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: device memory budget")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-rounds", type=int, default=2000,
-                    help="rounds of the CPU oracle timed for cpu_baseline")
+                    help="city/tiny: rounds of the CPU oracle timed for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-scan", action="store_true")
     ap.add_argument("--max-rounds", type=int, default=-1,
                     help="city/tiny, profiling only: stop every solve after this many rounds "
                          "(the line is then not a full-solve measurement)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -834,11 +845,476 @@ def run_road(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ headline ---
+
+HEADLINE_METRIC = "solves/s served vs sequential, bit-exact objective; scan GB/s vs HBM; p99 ms"
+WARM0 = 50_000          # warm-up requests come from stream indices beyond the timed ones
+
+
+def shard(seq, rank: int, world: int) -> list:
+    """Round-robin share of `rank` among `world` replicas.  Instances are
+    independent, so replicas split them without any data-path collective."""
+    return list(seq)[rank::world]
+
+
+def merge_shards(parts):
+    """Inverse of shard: the per-rank lists back in global order."""
+    world = len(parts)
+    total = sum(len(p) for p in parts)
+    return [parts[i % world][i // world] for i in range(total)]
+
+
+def parse_size(text: str):
+    n, k = (int(v) for v in text.lower().split("x"))
+    return n, k
+
+
+def warmup_indices(count: int, large) -> list:
+    """Small requests of the serving stream past the timed ones, to warm up."""
+    import lbdd_inputs as L
+    out, i = [], WARM0
+    while len(out) < count:
+        if not L.serve_recipe(i, large=large)[1]:
+            out.append(i)
+        i += 1
+    return out
+
+
+def oracle_sample(indices, large, limit_nk: int = 2_000_000) -> list:
+    """The stream requests among `indices` (in order) small enough for whole
+    oracle solves: n * k <= limit_nk."""
+    import lbdd_inputs as L
+    out = []
+    for i in indices:
+        r, big = L.serve_recipe(i, large=large)
+        if not big and r.n * r.k <= limit_nk:
+            out.append(i)
+    return out
+
+
+def fifo_latencies_ms(arrivals, service):
+    """Latencies of one server taking requests in arrival order, each for its
+    measured service time."""
+    done, out = 0.0, []
+    for a_t, s_t in zip(arrivals, service):
+        start = max(a_t, done)
+        done = start + s_t
+        out.append((done - a_t) * 1000.0)
+    return out
+
+
+def pct(values, q):
+    return float(np.percentile(np.asarray(values, dtype=np.float64), q)) if len(values) else None
+
+
+def serve_requests(lb, reqs, budget: int, quantum_us: int, arrivals=None):
+    """Serve reqs [(cm, cap, pen)] through one request server; `arrivals`
+    (seconds from the first submission) or all at once.  Returns the results
+    [(info, allotment)], latencies (ms), wall time (s) and server stats."""
+    with lb.Server(budget, quantum_us=quantum_us) as srv:
+        t0 = time.perf_counter()
+        tickets = []
+        for i, (cm, cap, pen) in enumerate(reqs):
+            if arrivals is not None:
+                dt = arrivals[i] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+            tickets.append(srv.submit(cm, cap, pen))
+        res = [srv.result(t) for t in tickets]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    lat = [(info.done_ns - info.submit_ns) / 1e6 for info, _ in res]
+    return res, lat, wall, st
+
+
+def all_reduce_sum(values, world: int, device="cuda"):
+    if world <= 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t.tolist()]
+
+
+def gather_lists(values, world: int):
+    if world <= 1:
+        return [list(values)]
+    import torch.distributed as dist
+    out = [None] * world
+    dist.all_gather_object(out, list(values))
+    return out
+
+
+def batch_measure(lb, rank: int, world: int, m: int = 256, seq_every: int = 8):
+    """The batched mix: this rank's round-robin share of the 256 instances in
+    one CUDA-graph replay (one warm-up replay first), against every
+    seq_every-th instance solved alone; objectives compared with the stored
+    oracle results."""
+    import torch
+    import lbdd_inputs as L
+    idx = shard(range(m), rank, world)
+    insts = [L.make(L.batch_recipe(i), dtype="i16") for i in idx]
+    solvers = [lb.Solver(x.cm, x.cap, x.pen) for x in insts]
+    lb.tune_clear()
+    batch = lb.Batch(solvers)
+    plan = batch.plan()[1]
+
+    def step():
+        for s in solvers:
+            lb.reset(s.h)
+        batch.run()
+    step()
+    torch.cuda.synchronize()
+    _barrier(world)
+    e0, e1 = _events()
+    e0.record()
+    step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    objectives = [s.objective for s in solvers]
+    with open(os.path.join(ROOT, "tests", "golden", f"batch{m}_oracle.json")) as f:
+        gold = {r["i"]: r["delta"] for r in json.load(f)["instances"]}
+    equal = all(gold[i] == o for i, o in zip(idx, objectives))
+    seq_ms, seq_n = 0.0, 0
+    for j in range(0, len(solvers), max(1, seq_every)):
+        s = solvers[j]
+        s.reset()
+        a, b = _events()
+        a.record()
+        s.solve()
+        b.record()
+        torch.cuda.synchronize()
+        seq_ms += a.elapsed_time(b)
+        seq_n += 1
+        assert s.objective == objectives[j], "batched and lone solves differ"
+    seq_ms, seq_n, eq_all = all_reduce_sum([seq_ms, seq_n, 1.0 if equal else 0.0], world)
+    batch.close()
+    for s in solvers:
+        s.close()
+    value = m / (ms / 1000.0)
+    seq = seq_n / (seq_ms / 1000.0)
+    return {"value": value, "unit": "solves/s", "instances": m, "ms_per_replay": ms,
+            "plan_groups_C_clusters_instances": plan,
+            "sequential": {"value": seq, "unit": "solves/s", "instances_timed": int(seq_n),
+                           "sample": f"every {seq_every}-th instance alone, default cluster size"},
+            "batched_over_sequential": value / seq,
+            "objectives_equal_oracle": eq_all == world,
+            "workload": f"batched mix of {m} instances, n log-uniform [1e3, 1e5), k log-uniform "
+                        "[10, 400), one CUDA-graph replay"}
+
+
+def scan_measure(lb, hbm_peak, peak_kind, reps: int = 20):
+    """Full best-transfer table (lbdd_best_transfer) of the s_min allotment of
+    the 2,000,000 x 2,000 instance, int16 (8 GB) and int32 (16 GB); bytes =
+    n*k*w + 4n per call; 20 timed calls after 3 warm-ups (inputs > L2)."""
+    import torch
+    import lbdd_inputs as L
+    inst = L.make_named("large", dtype="i16")
+    n, k = inst.n, inst.k
+    out = {}
+    for dt in ("i16", "i32"):
+        cmd = lb.CM_I16 if dt == "i16" else lb.CM_I32
+        ld = lb.cm_pitch(k, cmd)
+        tdt = torch.int16 if dt == "i16" else torch.int32
+        buf = torch.zeros(n * ld + 128, dtype=tdt, device="cuda")
+        src = torch.from_numpy(inst.cm.reshape(-1))
+        chunk = 1 << 28
+        for a in range(0, n * k, chunk):
+            b = min(a + chunk, n * k)
+            buf[a:b].copy_(src[a:b].cuda().to(tdt))
+        assign = torch.argmin(buf[: n * k].view(n, k), dim=1).to(torch.int32)
+        ms, tc, td = _scan_gbs(lb, buf, cmd, ld, n, k, assign, reps)
+        w = 2 if dt == "i16" else 4
+        byts = n * k * w + 4 * n
+        gbs = byts / ms / 1e6
+        out[dt] = {"kernel": "lbdd_best_transfer (all stages)", "bound": "hbm", "achieved": gbs,
+                   "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                   "peak_kind": peak_kind, "traffic": None, "ms": ms, "bytes": byts,
+                   "table_sha256": hashlib.sha256(tc.cpu().numpy().tobytes() +
+                                                  td.cpu().numpy().tobytes()).hexdigest()}
+        del buf, assign, tc, td
+        torch.cuda.empty_cache()
+    out["tables_equal_i16_i32"] = out["i16"]["table_sha256"] == out["i32"]["table_sha256"]
+    out["workload"] = ("s_min allotment of the 2,000,000 x 2,000 instance (clustered demand, "
+                       "road factors); CM 8 GB int16 / 16 GB int32, larger than L2")
+    return out
+
+
+def city_measure(lb, hbm_peak, peak_kind):
+    """One whole solve of the 200,000 x 500 city instance (a single persistent
+    launch), its objective against the stored whole-solve oracle result, and
+    the solver kernel's roofline (algorithmic CM bytes / launch time)."""
+    import torch
+    import lbdd_inputs as L
+    inst = L.make_named("city", dtype="i16")
+    cm_dev = torch.from_numpy(inst.cm).cuda()
+    solver = lb.Solver(cm_dev, inst.cap, inst.pen)
+    del cm_dev
+    stream = torch.cuda.current_stream()
+    solver.solve(0)                 # attributes, first launch
+    solver.reset()
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record(stream)
+    solver.solve()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = solver.stats()
+    obj = solver.objective
+    solver.close()
+    with open(os.path.join(ROOT, "tests", "golden", "city_oracle.json")) as f:
+        gold = json.load(f)
+    w = st.cm_elem_bytes
+    alg = (st.rows_scanned + 2 * inst.n) * inst.k * w + st.col_rows * 2 * w
+    achieved = alg / (ms / 1000.0) / 1e9
+    traffic = committed_traffic("asral_cluster_kernel", "city")
+    roof = {"kernel": "asral_cluster_kernel", "bound": "hbm", "achieved": achieved,
+            "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+            "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+            "algorithmic_bytes_per_launch": alg,
+            "note": "one launch = one whole city solve (200,000 rounds); latency bound "
+                    "(Bellman-Ford sweeps exchanging labels between the 16 CTAs of a cluster)"}
+    return {"value": 1000.0 / ms, "unit": "solves/s", "ms": ms, "us_per_round": 1000.0 * ms / inst.n,
+            "objective": obj, "objective_equals_oracle": obj == gold["delta"],
+            "bf_sweeps_per_round": st.bf_sweeps / inst.n, "cluster_size": st.cluster_size,
+            "workload": "city-scale single solve |D|=200,000 x |S|=500, CM int16 resident in HBM",
+            "roofline": roof}
+
+
+def oracle_headline_sample(sample, large, budget_s: float, results=None):
+    """The CPU oracle, single-threaded, solving whole requests of `sample` in
+    order until budget_s has passed; where `results` holds the served result
+    of a request, its objective and allotment must be the oracle's."""
+    import lbdd_inputs as L
+    import oracle
+    done, checked, t0 = 0, 0, time.perf_counter()
+    for i in sample:
+        x = L.make(L.serve_recipe(i, large=large)[0])
+        r = oracle.asral(x.cm, x.cap, x.pen, mode=oracle.MODE_HEAP)
+        assert r.rc == 0
+        done += 1
+        if results is not None and i in results:
+            obj, a = results[i]
+            assert obj == r.delta and np.array_equal(a, r.assign), f"request {i} differs from the oracle"
+            checked += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done, dt, checked
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    import torch
+    torch.cuda.synchronize()
+
+
+def run_headline(args):
+    """Default line: the serving stream (continuous batching through the
+    request server) against the same requests solved one at a time, with
+    p50/p99 latency; sub-keys for the batched mix, the HBM-bound scan, the
+    city solve (the solver's roofline) and the CPU oracle."""
+    import torch
+    import lbdd_inputs as L
+    import paper_2304_06543_gb300 as lb
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lb.load()
+    hbm_peak, peak_kind = peaks()
+    K, M, W = args.steps, args.per_step, args.warmup
+    large = parse_size(args.large)
+    R = K * M
+    mine = shard(range(R), rank, world)
+    recs = {i: L.serve_recipe(i, large=large) for i in mine}
+    insts = {i: L.make(r, dtype="i16") for i, (r, _) in recs.items()}
+    budget = int(args.budget_gb * (1 << 30))
+    dev = {i: torch.from_numpy(x.cm).cuda() for i, x in insts.items()}
+    dreq = [(dev[i], insts[i].cap, insts[i].pen) for i in mine]
+    hreq = [(insts[i].cm, insts[i].cap, insts[i].pen) for i in mine]
+    # cluster-size table on this share's own sizes (clones; outside every timed region)
+    tune = [lb.Solver(x.cm, x.cap, x.pen) for x in insts.values()]
+    lb.autotune(tune, probe_rounds=4096)
+    for s in tune:
+        s.close()
+    # warm-up: W steps of small requests that are not part of the timed stream
+    warm = shard(warmup_indices(W * M * world, large), rank, world)
+    wins = [L.make(L.serve_recipe(i, large=large)[0], dtype="i16") for i in warm]
+    serve_requests(lb, [(torch.from_numpy(x.cm).cuda(), x.cap, x.pen) for x in wins], budget,
+                   args.quantum_us)
+    # 1. timed: the K steps of the stream arrive at once, CMs resident in HBM
+    clocks = ClockSampler(local)
+    _barrier(world)
+    clocks.start()
+    e0, e1 = _events()
+    e0.record()
+    res, lat, wall, st = serve_requests(lb, dreq, budget, args.quantum_us)
+    torch.cuda.synchronize()
+    e1.record()
+    torch.cuda.synchronize()
+    _barrier(world)
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    value = R / (ms / 1000.0)
+    assert all(info.state == lb.REQ_DONE for info, _ in res)
+    served = {i: (info.objective, a) for i, (info, a) in zip(mine, res)}
+    sat_lat = merge_shards(gather_lists(lat, world))
+    launches = all_reduce_sum([st.launches], world)[0]
+    # 2. latency under Poisson arrivals at 0.9 x the saturated rate
+    rate = 0.9 * value
+    arr_all = L.arrival_times(R, rate)
+    arr = np.array([arr_all[i] for i in mine]) - (arr_all[mine[0]] if mine else 0.0)
+    res_p, lat_p, wall_p, st_p = serve_requests(lb, dreq, budget, args.quantum_us, arrivals=arr)
+    assert [info.objective for info, _ in res_p] == [served[i][0] for i in mine]
+    poi_lat = merge_shards(gather_lists(lat_p, world))
+    # 3. end to end: host CMs (copies to the device inside), allotments back to the host
+    _barrier(world)
+    t0 = time.perf_counter()
+    res_h, _, wall_h, _ = serve_requests(lb, hreq, budget, args.quantum_us)
+    _barrier(world)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) * 1000.0, world) / 1000.0
+    for i, (info, a) in zip(mine, res_h):
+        assert info.objective == served[i][0] and np.array_equal(a, served[i][1])
+    h2d = sum(all_reduce_sum([sum(insts[i].cm.nbytes + insts[i].cap.nbytes +
+                                  insts[i].pen.nbytes for i in mine)], world))
+    d2h = sum(all_reduce_sum([sum(4 * insts[i].n + 8 for i in mine)], world))
+    # 4. one at a time: each request alone (device-resident CM), in arrival order
+    service = []
+    for i in mine:
+        t0 = time.perf_counter()
+        s = lb.Solver(dev[i], insts[i].cap, insts[i].pen)
+        s.solve()
+        a = s.assignment()
+        obj = s.objective
+        s.close()
+        service.append(time.perf_counter() - t0)
+        assert obj == served[i][0] and np.array_equal(a, served[i][1]), "served and lone differ"
+    service_all = merge_shards(gather_lists(service, world))
+    seq = R / sum(service_all)          # one GPU solving the whole stream alone
+    seq_lat = fifo_latencies_ms(arr_all, service_all)
+    del dev, dreq
+    torch.cuda.empty_cache()
+    # 5. the batched mix, sharded like the stream
+    batched = batch_measure(lb, rank, world)
+    # 6. rank 0: the HBM-bound scan, the city solve, the CPU oracle
+    scan = city = cpu = None
+    if rank == 0:
+        scan = None if args.no_scan else scan_measure(lb, hbm_peak, peak_kind)
+        city = city_measure(lb, hbm_peak, peak_kind)
+        if not args.no_cpu:
+            sample = oracle_sample(mine, large)
+            n_done, secs, checked = oracle_headline_sample(sample, large, args.cpu_seconds, served)
+            cpu = {"value": n_done / secs, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                   "sample": f"the first {n_done} small requests of the stream (n*k <= 2e6), each "
+                             f"solved whole, heap mode, {secs:.1f} s; the served allotments and "
+                             f"objectives of {checked} of them equal the oracle's",
+                   "requests_checked_against_oracle": checked}
+    _barrier(world)
+    if rank == 0:
+        n_large = sum(1 for i in range(R) if L.serve_recipe(i, large=large)[1])
+        line = {
+            "metric": HEADLINE_METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int16",
+            "data": "synthetic (seeded generator; the paper's New Delhi road network is not "
+                    "available)",
+            "config": {"workload": f"serving stream of {R} requests ({M} per step, all arriving "
+                                   f"at once): 95% sized like the batched mix (n 1e3-1e5, k "
+                                   f"10-400), 5% large at {large[0]}x{large[1]}; CMs resident "
+                                   f"in device memory",
+                       "requests": R, "large_requests": n_large,
+                       "large_size": f"{large[0]}x{large[1]}", "budget_gb": args.budget_gb,
+                       "quantum_us": args.quantum_us,
+                       "l2": "inputs larger than L2 (CMs of the stream total "
+                             f"{h2d / 1e9:.2f} GB)",
+                       "parallelism": f"replicas x{world} (round-robin shares of the stream)"},
+            "served_over_sequential": value / seq,
+            "p50_ms": pct(poi_lat, 50), "p99_ms": pct(poi_lat, 99),
+            "served": {"solves_per_s": value, "wall_ms": ms, "p50_ms": pct(sat_lat, 50),
+                       "p99_ms": pct(sat_lat, 99), "passes": st.passes,
+                       "busy_frac": st.busy_ns / max(1, st.uptime_ns),
+                       "peak_active": st.peak_active, "peak_budget_gb": st.peak_bytes / 2**30},
+            "served_poisson": {"arrival_rate_per_s": rate, "rate_rule": "0.9 x saturated rate",
+                               "solves_per_s": R / max_over_ranks(wall_p * 1000, world) * 1000,
+                               "p50_ms": pct(poi_lat, 50), "p99_ms": pct(poi_lat, 99),
+                               "busy_frac": st_p.busy_ns / max(1, st_p.uptime_ns)},
+            "sequential": {"solves_per_s": seq, "p50_ms": pct(seq_lat, 50),
+                           "p99_ms": pct(seq_lat, 99),
+                           "rule": "each request alone through lbdd_create/solve from its "
+                                   "device-resident CM; FIFO latency from the same Poisson "
+                                   "arrivals and the measured service times"},
+            "e2e": {"value": R / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d / K,
+                    "d2h_bytes_per_step": d2h / K,
+                    "rule": "the same stream through lbdd_server_submit from host memory, "
+                            "allotments copied back"},
+            "objectives": "served = alone for every request; oracle-checked requests in "
+                          "cpu_baseline; batched mix vs stored oracle results in batched",
+            "batched": batched, "scan": scan, "city_solve": city,
+            "roofline": city["roofline"] if city else None,
+            "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference_headline(args):
+    """The oracle arm of the default workload: each step solves one whole
+    small request of the serving stream (the sample cpu_baseline uses), on
+    one host core; solves/s over the timed steps."""
+    import lbdd_inputs as L
+    import oracle
+    large = parse_size(args.large)
+    sample = oracle_sample(range(args.steps * args.per_step), large)
+    if not sample:
+        print(json.dumps({"impl": "reference", "unavailable": "no small request in the stream"}))
+        return
+    for w in range(args.warmup):
+        x = L.make(L.serve_recipe(sample[w % len(sample)], large=large)[0])
+        oracle.asral(x.cm, x.cap, x.pen, max_rounds=min(50, x.n))
+    times = []
+    for s in range(args.steps):
+        x = L.make(L.serve_recipe(sample[s % len(sample)], large=large)[0])
+        t0 = time.perf_counter()
+        r = oracle.asral(x.cm, x.cap, x.pen, mode=oracle.MODE_HEAP)
+        times.append(time.perf_counter() - t0)
+        assert r.rc == 0
+    value = len(times) / sum(times)
+    line = {"metric": HEADLINE_METRIC, "value": value, "unit": "solves/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"serving stream of {args.steps * args.per_step} requests "
+                                   f"({args.per_step} per step): 95% sized like the batched mix, "
+                                   f"5% large at {large[0]}x{large[1]}",
+                       "step": "one whole small request of the stream (n*k <= 2e6) solved by the "
+                               "CPU oracle; the large requests are not sampled"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(times)} whole small requests, heap mode"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, _ = dist_env()
     if args.impl == "reference":
-        run_reference(args)
+        if args.workload == "headline":
+            if rank == 0:
+                run_reference_headline(args)
+        else:
+            run_reference(args)
+    elif args.workload == "headline":
+        run_headline(args)
     elif args.workload not in ("city", "tiny") and world > 1 and rank != 0:
         return   # the batch / serve / large / road measurements run on rank 0 only
     elif args.workload == "batch":

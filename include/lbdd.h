@@ -234,11 +234,14 @@ int lbdd_tune_clear(void);
  * Solve requests of mixed sizes are admitted in arrival order while the
  * device-memory budget and the active-slot limit allow; admitted requests
  * keep CM, allotment and loads resident on the device and advance together
- * in time-sliced passes (the batch plan above, shortest remaining work
- * first, each pass ending after quantum_us); requests admitted during a
- * pass join the next one, finished ones are retired (allotment copied to the
- * caller's buffer, device memory freed) while others keep solving.  Each
- * result is bit-identical to the same instance solved alone. */
+ * in time-sliced passes (the batch plan above: SM shares in proportion to
+ * remaining work, shortest remaining work first within a cluster size;
+ * each pass ends after quantum_us); a request that made no progress for 8
+ * passes in a row goes first within its cluster size until it runs again.
+ * Requests admitted during a pass join the next one, finished ones are
+ * retired (allotment copied to the caller's buffer, device memory freed)
+ * while others keep solving.  Each result is bit-identical to the same
+ * instance solved alone. */
 typedef struct lbdd_server lbdd_server;
 typedef struct lbdd_server_config {
   size_t budget_bytes;   /* device bytes all admitted requests may hold */
@@ -272,6 +275,15 @@ int lbdd_server_create(lbdd_server** out, const lbdd_server_config* cfg);
 int lbdd_server_submit(lbdd_server* srv, int32_t n, int32_t k, const void* cm, int cm_dtype,
                        const int32_t* cap, const int32_t* pen, int32_t* assign_out,
                        int64_t* ticket);
+/* As lbdd_server_submit, with cm in device memory of the server's device
+ * when cm_is_device = 1 (0: host, the same as lbdd_server_submit).  A
+ * device cm must already hold its values when the call is made (work that
+ * writes it must have completed) and stay valid until the request is DONE
+ * or FAILED; admission copies it on the server's own stream.  Other
+ * values of cm_is_device return LBDD_ERR_ARG. */
+int lbdd_server_submit_ex(lbdd_server* srv, int32_t n, int32_t k, const void* cm, int cm_dtype,
+                          int cm_is_device, const int32_t* cap, const int32_t* pen,
+                          int32_t* assign_out, int64_t* ticket);
 /* Wait up to timeout_ms (< 0: forever, 0: do not wait) for a request to end;
  * fills *out either way.  LBDD_OK when it ended, LBDD_ERR_TIMEOUT if not. */
 int lbdd_server_poll(lbdd_server* srv, int64_t ticket, int64_t timeout_ms,

@@ -125,6 +125,8 @@ def load():
         lib.lbdd_tune_clear.argtypes = []
         lib.lbdd_server_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(_ServerConfig)]
         lib.lbdd_server_submit.argtypes = [P, i32, i32, P, c_int, P, P, P, ctypes.POINTER(i64)]
+        lib.lbdd_server_submit_ex.argtypes = [P, i32, i32, P, c_int, c_int, P, P, P,
+                                              ctypes.POINTER(i64)]
         lib.lbdd_server_poll.argtypes = [P, i64, i64, ctypes.POINTER(_RequestInfo)]
         lib.lbdd_server_release.argtypes = [P, i64]
         lib.lbdd_server_get_stats.argtypes = [P, ctypes.POINTER(_ServerStats)]
@@ -560,19 +562,29 @@ class Server:
         self.h = h
         self._bufs = {}
 
-    def submit(self, cm: np.ndarray, cap, pen) -> int:
-        cm = np.ascontiguousarray(cm)
-        dt = {np.dtype(np.int32): CM_I32, np.dtype(np.int16): CM_I16}[cm.dtype]
+    def submit(self, cm, cap, pen) -> int:
+        """Queue a request; cm is a host (n, k) array (lbdd_server_submit) or
+        a contiguous CUDA tensor whose values are ready (lbdd_server_submit_ex
+        with a device CM).  The binding keeps cm alive until the result is
+        taken."""
+        if isinstance(cm, np.ndarray):
+            cm = np.ascontiguousarray(cm)
+            dt = {np.dtype(np.int32): CM_I32, np.dtype(np.int16): CM_I16}[cm.dtype]
+            ptr, is_dev = cm.ctypes.data, 0
+        else:
+            import torch
+            dt = {torch.int32: CM_I32, torch.int16: CM_I16}[cm.dtype]
+            ptr, is_dev = _dptr(cm), 1
         if cm.ndim != 2:
-            raise ValueError(f"cm: expected an (n, k) matrix, got shape {cm.shape}")
-        n, k = cm.shape
+            raise ValueError(f"cm: expected an (n, k) matrix, got shape {tuple(cm.shape)}")
+        n, k = (int(x) for x in cm.shape)
         cap = _host_vec(cap, k, "cap")
         pen = _host_vec(pen, k, "pen")
         out = np.empty(n, np.int32)
         t = ctypes.c_int64()
-        _check(load().lbdd_server_submit(self.h, int(n), int(k), cm.ctypes.data, dt,
-                                         cap.ctypes.data, pen.ctypes.data, out.ctypes.data,
-                                         ctypes.byref(t)), "lbdd_server_submit")
+        _check(load().lbdd_server_submit_ex(self.h, n, k, ptr, dt, is_dev, cap.ctypes.data,
+                                            pen.ctypes.data, out.ctypes.data, ctypes.byref(t)),
+               "lbdd_server_submit_ex")
         self._bufs[t.value] = (cm, out)
         return t.value
 

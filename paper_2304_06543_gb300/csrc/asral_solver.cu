@@ -825,6 +825,180 @@ struct Solver {
     return result;
   }
 
+  // Relaxes the frontier entries slice, slice + step, ... (node order) into
+  // owned column cl, folding into (bl, bu) (one-CTA clusters).
+  template <bool STRICT, bool TSM>
+  __device__ __forceinline__ void relax_front(const Ent* fr, int nfront, int slice, int step,
+                                              int cl, bool colok, LT& bl, int32_t& bu) const {
+    constexpr int32_t inf = TSM ? kTsInf : kTInf;
+    constexpr int U = 4;
+    int f = slice;
+    for (; f + (U - 1) * step < nfront; f += U * step) {
+      Ent e[U];
+      int32_t t[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) e[q] = fr[f + q * step];
+#pragma unroll
+      for (int q = 0; q < U; ++q) t[q] = colok ? edge<TSM>(e[q].u, cl) : inf;
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        if (STRICT) t[q] = strict_cost(t[q], e[q].u, inf);
+        const LT c = e[q].l + (LT)t[q];
+        if (t[q] != inf && c < bl) { bl = c; bu = e[q].u; }
+      }
+    }
+    for (; f < nfront; f += step) {
+      const Ent e = fr[f];
+      int32_t t = colok ? edge<TSM>(e.u, cl) : inf;
+      if (STRICT) t = strict_cost(t, e.u, inf);
+      const LT c = e.l + (LT)t;
+      if (t != inf && c < bl) { bl = c; bu = e.u; }
+    }
+  }
+
+  // The same Bellman-Ford for a one-CTA cluster: no messages.  The frontier
+  // (the labels that improved in the last sweep, in node order) is one list
+  // in shared memory; the warps split into column blocks of 32 owned columns
+  // and, per block, into slices of the frontier; the slices' minima are
+  // combined per column, the improved labels recorded and compacted into
+  // the next frontier in node order.
+  __device__ int bellman_ford_1cta(int32_t j, bool npath, bool merged, bool allow_skip) {
+    Ent* fr = reinterpret_cast<Ent*>(s_inbox);   // the inbox is unused without peers
+    for (int cl = tid; cl < w; cl += kThreads) {
+      s_dist[cl] = kDInf;
+      s_hop[cl] = -1;
+      s_par[cl] = -1;
+    }
+    if (tid == 0) fr[0] = Ent{0, j};
+    __syncthreads();
+    const int32_t pen_j = npath ? qlast(j) : 0;
+    const bool strict = flags & OPT_STRICT;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int CB = max(1, (wr + 31) / 32);
+    const int WPB = max(1, kWarps / CB);
+    const int RS = w + 1;
+    uint64_t* red = reinterpret_cast<uint64_t*>(s_red);   // [WPB][RS] per-slice column minima
+    int* wcnt = s_tail;                                    // [kWarps] frontier counts
+    uint32_t lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    int64_t sink_dist = kDInf;
+    int32_t sink_par = -1;
+    int nfront = 1;
+    int result = 0;
+    for (int sweep = 1;; ++sweep) {
+      const bool tmr = timer();
+      const uint64_t t0 = tmr ? clock_cycles() : 0;
+      if (tmr) front_stat(nfront);
+      // relax: warp (block, slice) over its slice of the frontier
+      for (int bw = warp; bw < CB * WPB; bw += kWarps) {
+        const int blk = bw / WPB, slice = bw - blk * WPB;
+        const int cl = blk * 32 + lane;
+        LT bl = kNoLab;
+        int32_t bu = -1;
+        uint64_t key = ~0ull;
+        if (npath && c0 + cl == j) {   // Def. 10 (c): q_u() - q_{s*}()
+          for (int f = slice; f < nfront; f += WPB) {
+            const Ent e = fr[f];
+            if (e.u == j) continue;
+            const int64_t t = (int64_t)(s_slack[e.u] >= 0 ? s_pen[e.u] : 0) - pen_j;
+            key = min(key, pack_key((int64_t)e.l + t, e.u));
+          }
+        } else {
+          const bool colok = cl < wr;
+          if (tsm_on) {
+            if (strict) relax_front<true, true>(fr, nfront, slice, WPB, cl, colok, bl, bu);
+            else relax_front<false, true>(fr, nfront, slice, WPB, cl, colok, bl, bu);
+          } else {
+            if (strict) relax_front<true, false>(fr, nfront, slice, WPB, cl, colok, bl, bu);
+            else relax_front<false, false>(fr, nfront, slice, WPB, cl, colok, bl, bu);
+          }
+          if (bu >= 0) key = pack_key(bl, bu);
+        }
+        if (cl < w) red[slice * RS + cl] = key;
+      }
+      if (tmr) B->t_rloop += clock_cycles() - t0;
+      __syncthreads();
+      const uint64_t t1 = tmr ? clock_cycles() : 0;
+      // combine the slices per column, record, and compact the improved
+      // labels into the next frontier (node order: column order)
+      int total = 0;
+      bool sink_chg = false;
+      for (int base = 0; base < w; base += kThreads) {
+        const int cl = base + tid;
+        LT l = kNoLab;
+        if (cl < wr) {
+          uint64_t best = ~0ull;
+          for (int sl = 0; sl < WPB; ++sl) best = min(best, red[sl * RS + cl]);
+          if (c0 + cl == j) {   // the sink
+            if (best != ~0ull && key_label(best) < sink_dist) {
+              s_misc[MS_SINK_IN] = (int64_t)best;
+              sink_chg = true;
+            }
+          } else if (best != ~0ull) {
+            const int64_t bc = key_label(best);
+            if (bc < s_dist[cl]) {
+              s_dist[cl] = bc;
+              s_hop[cl] = sweep;
+              s_par[cl] = (int32_t)(best & 0xffffu);
+              l = (LT)bc;
+            }
+          }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, l != kNoLab);
+        if (lane == 0) wcnt[warp] = __popc(m);
+        sink_chg = __syncthreads_or(sink_chg) != 0 || sink_chg;
+        const int wc = lane < kWarps ? wcnt[lane] : 0;
+        int incl = wc;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const int o = __shfl_up_sync(0xffffffffu, incl, off);
+          if (lane >= off) incl += o;
+        }
+        const int at = total + __shfl_sync(0xffffffffu, incl - wc, warp);
+        if (l != kNoLab) fr[at + __popc(m & lt)] = Ent{l, c0 + cl};
+        total += __shfl_sync(0xffffffffu, incl, kWarps - 1);
+        __syncthreads();   // counts read before the next chunk rewrites them
+      }
+      if (sink_chg) {
+        const uint64_t sk = (uint64_t)s_misc[MS_SINK_IN];
+        sink_dist = key_label(sk);
+        sink_par = (int32_t)(sk & 0xffffu);
+      }
+      if (tmr) {
+        const uint64_t t2 = clock_cycles();
+        B->t_relax += t1 - t0;
+        B->t_sync += t2 - t1;
+      }
+      if (sweep == 1) commit_pending();
+      if (sweep == 1 && allow_skip && !merged) {
+        // T is unchanged since the last round, whose Gamma had no negative
+        // cycle (Lemmas 1/2): the NegCycle sink label cannot be negative.
+        if (tid == 0) B->skipped++;
+        result = 0;
+        if (tid == 0) s_misc[MS_MERGE_ANY] = 0;
+        break;
+      }
+      if (total == 0 && !sink_chg) {
+        if (tid == 0) {
+          B->bf_calls++;
+          B->bf_sweeps += sweep;
+          B->bf_max = max(B->bf_max, (int64_t)sweep);
+          s_misc[MS_MERGE_ANY] = 1;
+        }
+        result = sink_dist < 0 ? 1 : 0;
+        break;
+      }
+      if (sweep >= k + 1) { result = -1; break; }
+      nfront = total;
+    }
+    if (tid == 0) {
+      s_misc[MS_SINK_DIST] = sink_dist;
+      s_misc[MS_SINK_PAR] = sink_par;
+    }
+    __syncthreads();
+    return result;
+  }
+
   // Alg. 4 right after an Alg. 1 that applied nothing: T and the loads are
   // unchanged, and the NPath graph differs from the NCyc graph only in the
   // edges into the sink, which have no successors.  The converged node
@@ -1141,7 +1315,8 @@ struct Solver {
       // Alg. 1 at j
       pending_d = d;
       pending_j = j;
-      int res = bellman_ford(j, false, merged, allow_skip);
+      int res = C == 1 ? bellman_ford_1cta(j, false, merged, allow_skip)
+                       : bellman_ford(j, false, merged, allow_skip);
       if (res < 0) { status = res == -2 ? ST_ERR_TIMEOUT : ST_ERR_INVARIANT; break; }
       // labels converged (not skipped) and nothing applied: Alg. 4 can reuse them
       const bool reusable = (s_misc[MS_MERGE_ANY] != 0 || !allow_skip) && res == 0;
@@ -1153,7 +1328,8 @@ struct Solver {
       // Alg. 4 at j when the allotment overloaded it
       if (over) {
         res = reusable && !(flags & OPT_NO_NPATH_REUSE) ? npath_from_ncyc(j)
-                                                         : bellman_ford(j, true, true, false);
+              : C == 1 ? bellman_ford_1cta(j, true, true, false)
+                       : bellman_ford(j, true, true, false);
         if (res < 0) { status = res == -2 ? ST_ERR_TIMEOUT : ST_ERR_INVARIANT; break; }
         if (res > 0) {
           const int m = walk_path(j);

@@ -149,7 +149,8 @@ enum Order { LONGEST_FIRST = 0, SHORTEST_FIRST = 1 };
 
 // Groups of instances with equal (cost width, cluster size, options).
 static int build_groups(lbdd_solver* const* v, const int64_t* rem, int m,
-                        const std::vector<Est>& est, Order order, std::vector<Group>* groups) {
+                        const std::vector<Est>& est, Order order, const uint8_t* first,
+                        std::vector<Group>* groups) {
   groups->clear();
   for (int i = 0; i < m; ++i) {
     Group* g = nullptr;
@@ -168,11 +169,14 @@ static int build_groups(lbdd_solver* const* v, const int64_t* rem, int m,
     g->work += len * est[i].C;
     g->longest = std::max(g->longest, len);
   }
-  // heaviest group first; inside a group, longest (or shortest) instance first
+  // heaviest group first; inside a group the instances marked `first`, then
+  // longest (or shortest) instance first
   std::stable_sort(groups->begin(), groups->end(),
                    [](const Group& a, const Group& b) { return a.work > b.work; });
   for (auto& g : *groups) {
     std::stable_sort(g.idx.begin(), g.idx.end(), [&](int a, int b) {
+      const bool fa = first && first[a], fb = first && first[b];
+      if (fa != fb) return fa;
       const double la = (double)rem[a] * est[a].t, lb = (double)rem[b] * est[b].t;
       return order == LONGEST_FIRST ? la > lb : la < lb;
     });
@@ -240,8 +244,8 @@ static int allocate_proportional(std::vector<Group>* groups, int max_clusters, i
 // round, long instances moved to faster clusters, SMs shared in proportion
 // to estimated SM-time.
 static int make_plan(lbdd_solver* const* v, const int64_t* rem, int m, int forced_C,
-                     int max_clusters, int dev, int sms, Order order, std::vector<Group>* groups,
-                     std::vector<int>* cluster_of) {
+                     int max_clusters, int dev, int sms, Order order, const uint8_t* first,
+                     std::vector<Group>* groups, std::vector<int>* cluster_of) {
   std::vector<Est> est;
   Cands cands;
   int rc = choose_sizes(v, m, forced_C, dev, &est, &cands);
@@ -264,7 +268,7 @@ static int make_plan(lbdd_solver* const* v, const int64_t* rem, int m, int force
     if (next.C == 0) { cands[top].clear(); continue; }
     est[top] = next;
   }
-  rc = build_groups(v, rem, m, est, order, groups);
+  rc = build_groups(v, rem, m, est, order, first, groups);
   if (!rc) rc = allocate_proportional(groups, max_clusters, sms);
   if (rc) return rc;
   cluster_of->assign(m, 0);
@@ -385,7 +389,7 @@ int batch_alloc(lbdd_batch** out, int capacity, uint64_t quantum_ns, void* strea
 // and stages their instance records on b->st.  Every solver must live on
 // the batch's device.
 int batch_set(lbdd_batch* b, lbdd_solver* const* solvers, const int64_t* rem, int m,
-              int cluster_size, int max_clusters, bool shortest_first) {
+              int cluster_size, int max_clusters, bool shortest_first, const uint8_t* first) {
   if (!b || !solvers || m < 1 || m > b->capacity || cluster_size < 0 || cluster_size > 16 ||
       max_clusters < 0 || (cluster_size & (cluster_size - 1)) != 0)
     return LBDD_ERR_ARG;
@@ -396,7 +400,8 @@ int batch_set(lbdd_batch* b, lbdd_solver* const* solvers, const int64_t* rem, in
   }
   b->solvers.assign(solvers, solvers + m);
   int rc = make_plan(solvers, r.data(), m, cluster_size, max_clusters, b->dev, b->sms,
-                     shortest_first ? SHORTEST_FIRST : LONGEST_FIRST, &b->groups, &b->cluster_of);
+                     shortest_first ? SHORTEST_FIRST : LONGEST_FIRST, first, &b->groups,
+                     &b->cluster_of);
   if (rc) return rc;
   if (b->groups.size() > (size_t)kMaxGroups) return LBDD_ERR_ARG;
   b->slot_of.assign(m, 0);
@@ -478,7 +483,7 @@ extern "C" int lbdd_batch_create(lbdd_batch** out, lbdd_solver* const* solvers, 
   lbdd_batch* b = nullptr;
   int rc = batch_alloc(&b, m, 0, stream);
   if (rc) return rc;
-  rc = batch_set(b, solvers, nullptr, m, cluster_size, max_clusters, false);
+  rc = batch_set(b, solvers, nullptr, m, cluster_size, max_clusters, false, nullptr);
   if (!rc) rc = batch_capture(b);
   if (rc) { batch_free(b); return rc; }
   *out = b;
@@ -516,7 +521,7 @@ extern "C" int lbdd_solve_batch(lbdd_solver* const* solvers, int m, int64_t max_
   lbdd_batch* b = nullptr;
   int rc = batch_alloc(&b, m, 0, stream);
   if (rc) return rc;
-  rc = batch_set(b, solvers, nullptr, m, cluster_size, max_clusters, false);
+  rc = batch_set(b, solvers, nullptr, m, cluster_size, max_clusters, false, nullptr);
   int first = LBDD_OK;
   if (!rc) rc = batch_launch(b, max_rounds);
   if (!rc) rc = batch_wait(b, &first);

@@ -10,12 +10,16 @@
 //  * retirement copies a finished request's allotment and objective back,
 //    frees its solver and releases its budget, on a stream of its own;
 //  * the pass engine repeatedly runs one time-sliced pass over every active
-//    request: a batch plan (cluster size per request, SM shares per group,
-//    shortest remaining work first) and the persistent launches of
-//    lbdd_batch.cu with a quantum, after which every cluster stops at its
-//    next quantum check.  Solver state stays on the device between passes,
-//    so a request resumes exactly where it stopped; requests admitted during
-//    a pass join the next one.
+//    request: a batch plan (cluster size per request, SM shares per group in
+//    proportion to remaining work, shortest remaining work first inside a
+//    group) and the persistent launches of lbdd_batch.cu with a quantum,
+//    after which every cluster stops at its next quantum check.  A request
+//    that made no progress in kAgePasses passes in a row (its group had
+//    fewer clusters than instances and shorter ones kept them) moves to the
+//    front of its group until it runs again, so no request waits without
+//    bound.  Solver state stays on the device between passes, so a request
+//    resumes exactly where it stopped; requests admitted during a pass join
+//    the next one.
 //
 // A request's result does not depend on what it shares the GPU with: each
 // solve is a deterministic function of its own instance (canonical
@@ -39,7 +43,7 @@ using namespace lbdd;
 namespace lbdd {
 int batch_alloc(lbdd_batch** out, int capacity, uint64_t quantum_ns, void* stream);
 int batch_set(lbdd_batch* b, lbdd_solver* const* solvers, const int64_t* rem, int m,
-              int cluster_size, int max_clusters, bool shortest_first);
+              int cluster_size, int max_clusters, bool shortest_first, const uint8_t* first);
 int batch_launch(lbdd_batch* b, int64_t max_rounds);
 int batch_wait(lbdd_batch* b, int* first_rc);
 int batch_launches(const lbdd_batch* b);
@@ -52,16 +56,21 @@ namespace {
 
 enum State { QUEUED = 0, ACTIVE = 1, DONE = 2, FAILED = 3 };
 
+// Passes without progress after which a request goes first in its group.
+constexpr int kAgePasses = 8;
+
 struct Request {
   int64_t id = 0;
   int32_t n = 0, k = 0;
   const void* cm = nullptr;
   int dtype = LBDD_CM_I32;
+  int cm_is_device = 0;
   std::vector<int32_t> cap, pen;
   int32_t* assign_out = nullptr;
   size_t footprint = 0;
   lbdd_solver* solver = nullptr;
   int64_t rounds = 0;
+  int stalled = 0;        // passes in a row without progress
   int state = QUEUED;
   int status = LBDD_OK;
   int64_t objective = 0;
@@ -185,8 +194,8 @@ static void admit_loop(lbdd_server* S) {
     }
     lk.unlock();
     lbdd_solver* s = nullptr;
-    const int rc = lbdd_create(&s, r->n, r->k, r->cm, r->dtype, 0, r->cap.data(), r->pen.data(),
-                               S->admit_st);
+    const int rc = lbdd_create(&s, r->n, r->k, r->cm, r->dtype, r->cm_is_device, r->cap.data(),
+                               r->pen.data(), S->admit_st);
     lk.lock();
     if (rc) {
       S->bytes -= r->footprint;
@@ -209,6 +218,7 @@ static void engine_loop(lbdd_server* S) {
   std::vector<Request*> active;
   std::vector<lbdd_solver*> v;
   std::vector<int64_t> rem;
+  std::vector<uint8_t> aged;
   std::unique_lock<std::mutex> lk(S->mu);
   for (;;) {
     if (S->stop) break;   // unfinished requests are released by lbdd_server_destroy
@@ -222,12 +232,15 @@ static void engine_loop(lbdd_server* S) {
     lk.unlock();
     v.clear();
     rem.clear();
+    aged.clear();
     for (Request* r : active) {
       v.push_back(r->solver);
       rem.push_back(r->n - r->rounds);
+      aged.push_back(r->stalled >= kAgePasses ? 1 : 0);
     }
     const int64_t t_a = now_ns(S->t0);
-    int rc = batch_set(S->batch, v.data(), rem.data(), (int)v.size(), S->cfg.cluster_size, 0, true);
+    int rc = batch_set(S->batch, v.data(), rem.data(), (int)v.size(), S->cfg.cluster_size, 0, true,
+                       aged.data());
     if (!rc) rc = batch_launch(S->batch, -1);
     int first = LBDD_OK;
     if (!rc) rc = batch_wait(S->batch, &first);
@@ -241,7 +254,9 @@ static void engine_loop(lbdd_server* S) {
       Request* r = active[i];
       int st = rc;
       if (!rc) {
+        const int64_t before = r->rounds;
         r->rounds = batch_rounds(S->batch, (int)i);
+        r->stalled = r->rounds > before ? 0 : r->stalled + 1;
         st = status_to_rc(batch_status(S->batch, (int)i));
       }
       if (st != LBDD_OK || r->rounds >= r->n) {
@@ -293,10 +308,17 @@ extern "C" int lbdd_server_create(lbdd_server** out, const lbdd_server_config* c
 extern "C" int lbdd_server_submit(lbdd_server* S, int32_t n, int32_t k, const void* cm,
                                   int cm_dtype, const int32_t* cap, const int32_t* pen,
                                   int32_t* assign_out, int64_t* ticket) {
+  return lbdd_server_submit_ex(S, n, k, cm, cm_dtype, 0, cap, pen, assign_out, ticket);
+}
+
+extern "C" int lbdd_server_submit_ex(lbdd_server* S, int32_t n, int32_t k, const void* cm,
+                                     int cm_dtype, int cm_is_device, const int32_t* cap,
+                                     const int32_t* pen, int32_t* assign_out, int64_t* ticket) {
   if (!S || !ticket || n < 1 || k < 1 || k > lbdd_max_centers() || !cm || !cap || !pen ||
       !assign_out)
     return LBDD_ERR_ARG;
   if (cm_dtype != LBDD_CM_I32 && cm_dtype != LBDD_CM_I16) return LBDD_ERR_ARG;
+  if (cm_is_device != 0 && cm_is_device != 1) return LBDD_ERR_ARG;
   for (int32_t i = 0; i < k; ++i)
     if (cap[i] < 1 || pen[i] < 1) return LBDD_ERR_ARG;
   Request* r = new (std::nothrow) Request();
@@ -305,6 +327,7 @@ extern "C" int lbdd_server_submit(lbdd_server* S, int32_t n, int32_t k, const vo
   r->k = k;
   r->cm = cm;
   r->dtype = cm_dtype;
+  r->cm_is_device = cm_is_device;
   r->cap.assign(cap, cap + k);
   r->pen.assign(pen, pen + k);
   r->assign_out = assign_out;

@@ -91,3 +91,47 @@ def test_destroy_with_work_outstanding(gpu_lib, reqs):
     for x in insts:
         srv.submit(x.cm, x.cap, x.pen)
     srv.close()                       # returns: queued requests dropped, pass ends at its quantum
+
+
+def test_device_resident_requests_and_aging(gpu_lib, reqs):
+    """Requests whose CM is already in device memory (lbdd_server_submit_ex)
+    give the oracle's results.  Then a long request shares one cluster-size
+    group (16 CTAs forced) with twelve short ones under a 100 us quantum, so
+    shortest-first ordering and aging both reorder the group between passes;
+    every result is still the oracle's."""
+    import torch
+    insts, refs = reqs
+    with gpu_lib.Server(budget_bytes=8 << 30, max_active=12, quantum_us=300) as srv:
+        tickets = [srv.submit(torch.from_numpy(x.cm).cuda(), x.cap, x.pen) for x in insts[:8]]
+        for i, t in enumerate(tickets):
+            info, a = srv.result(t, TIMEOUT_MS)
+            assert info.state == gpu_lib.REQ_DONE and info.status == 0
+            assert info.objective == refs[i].delta and np.array_equal(a, refs[i].assign)
+    big = L.make(L.Recipe(n=6000, k=300, seed=4242, cap_frac=0.8, pen=(50, 500), name="big"),
+                 dtype="i16")
+    small = [L.make(L.Recipe(n=600, k=300, seed=4300 + i, cap_frac=0.8, pen=(50, 500),
+                             name=f"s{i}"), dtype="i16") for i in range(12)]
+    ref_big = oracle.asral(big.cm, big.cap, big.pen)
+    refs_small = [oracle.asral(x.cm, x.cap, x.pen) for x in small]
+    with gpu_lib.Server(budget_bytes=8 << 30, quantum_us=100, cluster_size=16) as srv:
+        tb = srv.submit(big.cm, big.cap, big.pen)
+        ts = [srv.submit(x.cm, x.cap, x.pen) for x in small]
+        info, a = srv.result(tb, TIMEOUT_MS)
+        assert info.objective == ref_big.delta and np.array_equal(a, ref_big.assign)
+        for t, r in zip(ts, refs_small):
+            info, a = srv.result(t, TIMEOUT_MS)
+            assert info.objective == r.delta and np.array_equal(a, r.assign)
+
+
+def test_submit_ex_rejects_bad_location_flag(gpu_lib):
+    import ctypes
+    x = L.random_small(10, n=50, k=4)
+    lib = gpu_lib.load()
+    out = np.empty(50, np.int32)
+    t = ctypes.c_int64()
+    cap, pen = x.cap.astype(np.int32), x.pen.astype(np.int32)
+    with gpu_lib.Server(budget_bytes=1 << 30) as srv:
+        rc = lib.lbdd_server_submit_ex(srv.h, 50, 4, x.cm.ctypes.data, gpu_lib.CM_I32, 2,
+                                       cap.ctypes.data, pen.ctypes.data, out.ctypes.data,
+                                       ctypes.byref(t))
+        assert rc == gpu_lib.ERR_ARG
