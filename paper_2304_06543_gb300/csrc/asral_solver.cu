@@ -690,49 +690,117 @@ struct Solver {
       if (sweep > 1 && src != rank) wait_message(q, src, sub == 0);
       uint64_t skey = ~0ull;     // this warp's best NPath sink candidate
       int cnt = 0;               // improved labels of the sender (sub 0)
-      const int nsb = sweep > 1 ? (w + 31) / 32 : 1;
-      for (int cb = 0; cb < ncb; ++cb) {
-        const int cl = cb * 32 + lane;
-        const bool colok = cl < wr && !(sink_here && c0 + cl == j);
-        LT bl = kNoLab;
-        int32_t bu = -1;
-        for (int sb = 0; sb < nsb; ++sb) {
-          LT l = 0;
-          bool valid = lane == 0 && src == 0;   // sweep 1: the source alone
-          if (sweep > 1) {
-            const int s = sb * 32 + lane;
-            l = s < w ? labs[s] : kNoLab;
-            valid = l != kNoLab;
+      if (WPS == 1) {
+        // one warp per sender: per column block and 32-slot block, the
+        // sender's labels are compacted into the warp's list and relaxed
+        const int nsb = sweep > 1 ? (w + 31) / 32 : 1;
+        for (int cb = 0; cb < ncb; ++cb) {
+          const int cl = cb * 32 + lane;
+          const bool colok = cl < wr && !(sink_here && c0 + cl == j);
+          LT bl = kNoLab;
+          int32_t bu = -1;
+          for (int sb = 0; sb < nsb; ++sb) {
+            LT l = 0;
+            bool valid = lane == 0 && src == 0;   // sweep 1: the source alone
+            if (sweep > 1) {
+              const int s = sb * 32 + lane;
+              l = s < w ? labs[s] : kNoLab;
+              valid = l != kNoLab;
+            }
+            unsigned bits = __ballot_sync(0xffffffffu, valid);
+            if (cb == 0) cnt += __popc(bits);
+            if (WPS > 1) {   // the sender's entries are shared among its warps
+              valid = valid && (int)(__popc(bits & lt) % WPS) == sub;
+              bits = __ballot_sync(0xffffffffu, valid);
+            }
+            const int32_t u = (sweep > 1 ? src * w + sb * 32 : j) + lane;
+            if (cb == 0 && sink_here) {   // Def. 10 (c): q_u() - q_{s*}()
+              uint64_t key = ~0ull;
+              if (valid && u != j) key = pack_key((int64_t)l + (s_slack[u] >= 0 ? s_pen[u] : 0) - pen_j, u);
+  #pragma unroll
+              for (int off = 16; off > 0; off >>= 1)
+                key = min(key, (uint64_t)__shfl_xor_sync(0xffffffffu, key, off));
+              skey = min(skey, key);
+            }
+            const int n = __popc(bits);
+            if (n == 0) continue;
+            __syncwarp();   // earlier reads of the list are done
+            if (valid) el[__popc(bits & lt)] = Ent{l, u};
+            __syncwarp();
+            if (tsm_on) {
+              if (strict) relax_list<true, true>(el, n, cl, colok, bl, bu);
+              else relax_list<false, true>(el, n, cl, colok, bl, bu);
+            } else {
+              if (strict) relax_list<true, false>(el, n, cl, colok, bl, bu);
+              else relax_list<false, false>(el, n, cl, colok, bl, bu);
+            }
           }
-          unsigned bits = __ballot_sync(0xffffffffu, valid);
-          if (cb == 0) cnt += __popc(bits);
-          if (WPS > 1) {   // the sender's entries are shared among its warps
-            valid = valid && (int)(__popc(bits & lt) % WPS) == sub;
-            bits = __ballot_sync(0xffffffffu, valid);
-          }
-          const int32_t u = (sweep > 1 ? src * w + sb * 32 : j) + lane;
-          if (cb == 0 && sink_here) {   // Def. 10 (c): q_u() - q_{s*}()
-            uint64_t key = ~0ull;
-            if (valid && u != j) key = pack_key((int64_t)l + (s_slack[u] >= 0 ? s_pen[u] : 0) - pen_j, u);
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1)
-              key = min(key, (uint64_t)__shfl_xor_sync(0xffffffffu, key, off));
-            skey = min(skey, key);
-          }
-          const int n = __popc(bits);
-          if (n == 0) continue;
+          if (cl < w) red[warp * RS + cl] = bu < 0 ? ~0ull : pack_key(bl, bu);
+        }
+      } else {
+        // The sender's slots in groups of 32 * WPS: each group's entries are
+        // dealt round-robin to the sender's WPS warps (at most 32 each), put
+        // into the warp's list once, and relaxed into every owned column block;
+        // the warp's row of `red` keeps its minimum per column (stored once
+        // when there is one group, the usual case of 32 columns per CTA).
+        const int gslots = 32 * WPS;
+        const int ngroups = sweep > 1 ? (w + gslots - 1) / gslots : 1;
+        if (ngroups > 1)
+          for (int cl = lane; cl < w; cl += 32) red[warp * RS + cl] = ~0ull;
+        for (int g = 0; g < ngroups; ++g) {
+          int n = 0, seen = 0;
           __syncwarp();   // earlier reads of the list are done
-          if (valid) el[__popc(bits & lt)] = Ent{l, u};
+          for (int sb = g * gslots; sb < min(w, (g + 1) * gslots) || (sweep == 1 && sb == 0);
+               sb += 32) {
+            LT l = 0;
+            bool valid = lane == 0 && src == 0;   // sweep 1: the source alone
+            if (sweep > 1) {
+              const int s = sb + lane;
+              l = s < w ? labs[s] : kNoLab;
+              valid = l != kNoLab;
+            }
+            const unsigned bits = __ballot_sync(0xffffffffu, valid);
+            cnt += __popc(bits);
+            const bool mine = valid && (int)((seen + __popc(bits & lt)) & (WPS - 1)) == sub;
+            seen += __popc(bits);
+            const unsigned mb = __ballot_sync(0xffffffffu, mine);
+            const int32_t u = (sweep > 1 ? src * w + sb : j) + lane;
+            if (mine) el[n + __popc(mb & lt)] = Ent{l, u};
+            n += __popc(mb);
+            if (sink_here) {   // Def. 10 (c): q_u() - q_{s*}()
+              uint64_t key = ~0ull;
+              if (mine && u != j) key = pack_key((int64_t)l + (s_slack[u] >= 0 ? s_pen[u] : 0) - pen_j, u);
+  #pragma unroll
+              for (int off = 16; off > 0; off >>= 1)
+                key = min(key, (uint64_t)__shfl_xor_sync(0xffffffffu, key, off));
+              skey = min(skey, key);
+            }
+            if (sweep == 1) break;
+          }
           __syncwarp();
-          if (tsm_on) {
-            if (strict) relax_list<true, true>(el, n, cl, colok, bl, bu);
-            else relax_list<false, true>(el, n, cl, colok, bl, bu);
-          } else {
-            if (strict) relax_list<true, false>(el, n, cl, colok, bl, bu);
-            else relax_list<false, false>(el, n, cl, colok, bl, bu);
+          if (n == 0) {
+            if (ngroups == 1)
+              for (int cl = lane; cl < w; cl += 32) red[warp * RS + cl] = ~0ull;
+            continue;
+          }
+          for (int cb = 0; cb < ncb; ++cb) {
+            const int cl = cb * 32 + lane;
+            const bool colok = cl < wr && !(sink_here && c0 + cl == j);
+            LT bl = kNoLab;
+            int32_t bu = -1;
+            if (tsm_on) {
+              if (strict) relax_list<true, true>(el, n, cl, colok, bl, bu);
+              else relax_list<false, true>(el, n, cl, colok, bl, bu);
+            } else {
+              if (strict) relax_list<true, false>(el, n, cl, colok, bl, bu);
+              else relax_list<false, false>(el, n, cl, colok, bl, bu);
+            }
+            if (cl < w) {
+              const uint64_t key = bu < 0 ? ~0ull : pack_key(bl, bu);
+              red[warp * RS + cl] = ngroups == 1 ? key : min(red[warp * RS + cl], key);
+            }
           }
         }
-        if (cl < w) red[warp * RS + cl] = bu < 0 ? ~0ull : pack_key(bl, bu);
       }
       if (lane == 0) s_rsink[warp] = skey;
       if (sweep > 1 && sub == 0 && lane == 0) {   // the sender's tail, for the decisions
