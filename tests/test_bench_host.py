@@ -95,3 +95,26 @@ def test_recorded_full_solve_time_comes_from_the_golden():
     assert rec["seconds"] == gold["oracle_seconds"] and rec["seconds"] > 1000
     assert bench.recorded_full_solve("city", SimpleNamespace(n=1000)) is None   # other size
     assert bench.recorded_full_solve("no_such_workload", SimpleNamespace(n=5)) is None
+
+
+def test_reference_arm_headline_line():
+    """The default workload's oracle arm: whole small requests of the serving
+    stream on one core, with the headline metric and config."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "2", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.HEADLINE_METRIC
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1
+    assert "serving stream of 8 requests" in d["config"]["workload"]
+    assert d["cpu_baseline"]["cores"] == 1 and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_default_arguments():
+    a = bench.parse([])
+    assert (a.workload, a.steps, a.per_step, a.large) == ("headline", 20, 4, "100000x1000")
+    assert a.warmup >= 3
