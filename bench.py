@@ -76,6 +76,8 @@ def parse(argv=None):
                     help="city/tiny: rounds of the CPU oracle timed for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-scan", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="headline: skip the batched mix")
+    ap.add_argument("--no-city", action="store_true", help="headline: skip the city solve")
     ap.add_argument("--max-rounds", type=int, default=-1,
                     help="city/tiny, profiling only: stop every solve after this many rounds "
                          "(the line is then not a full-solve measurement)")
@@ -1209,12 +1211,12 @@ def run_headline(args):
     del dev, dreq
     torch.cuda.empty_cache()
     # 5. the batched mix, sharded like the stream
-    batched = batch_measure(lb, rank, world)
+    batched = None if args.no_batch else batch_measure(lb, rank, world)
     # 6. rank 0: the HBM-bound scan, the city solve, the CPU oracle
     scan = city = cpu = None
     if rank == 0:
         scan = None if args.no_scan else scan_measure(lb, hbm_peak, peak_kind)
-        city = city_measure(lb, hbm_peak, peak_kind)
+        city = None if args.no_city else city_measure(lb, hbm_peak, peak_kind)
         if not args.no_cpu:
             sample = oracle_sample(mine, large)
             n_done, secs, checked = oracle_headline_sample(sample, large, args.cpu_seconds, served)
