@@ -55,6 +55,8 @@ def _load():
         lib.oracle_has_negative_cycle.argtypes = [i64, P]
         lib.oracle_asral.argtypes = [i64, i64, P, P, P, c_int, i64, c_int, P, P, P, P]
         lib.oracle_asral_q.argtypes = [i64, i64, P, P, P, i64, c_int, i64, c_int, P, P, P, P]
+        lib.oracle_asral_order.argtypes = [i64, i64, P, P, P, i64, c_int, i64, c_int, P, P, P, P,
+                                           P]
         lib.oracle_road_cm.argtypes = [i64, P, P, P, i64, P, i64, P, P]
         lib.oracle_objective_q.argtypes = [i64, i64, P, P, P, i64, P]
         lib.oracle_objective_q.restype = i64
@@ -128,8 +130,9 @@ def objective(cm, cap, pen, assign) -> int:
                                          _p(_c(pen, np.int32)), _p(_c(assign, np.int32))))
 
 
-def asral(cm, cap, pen, mode=MODE_HEAP, max_rounds=-1, check=False) -> Result:
-    """Alg. 2 on the instance; see asral_oracle.c for the exact reading."""
+def asral(cm, cap, pen, mode=MODE_HEAP, max_rounds=-1, check=False, order=None) -> Result:
+    """Alg. 2 on the instance; see asral_oracle.c for the exact reading.
+    order: the units' extraction order (default: the MinDistance order)."""
     cm = _c(cm, np.int32)
     n, k = cm.shape
     cap = _c(cap, np.int32)
@@ -138,11 +141,31 @@ def asral(cm, cap, pen, mode=MODE_HEAP, max_rounds=-1, check=False) -> Result:
     load = np.empty(k, np.int64)
     delta = ctypes.c_int64(0)
     st = _Stats()
-    rc = _load().oracle_asral(n, k, _p(cm), _p(cap), _p(pen), int(mode), int(max_rounds),
-                              int(bool(check)), _p(assign), _p(load), ctypes.byref(delta),
-                              ctypes.byref(st))
+    if order is None:
+        rc = _load().oracle_asral(n, k, _p(cm), _p(cap), _p(pen), int(mode), int(max_rounds),
+                                  int(bool(check)), _p(assign), _p(load), ctypes.byref(delta),
+                                  ctypes.byref(st))
+    else:
+        order = _c(order, np.int32)
+        if order.shape != (n,):
+            raise ValueError(f"order: expected {n} entries, got shape {order.shape}")
+        rc = _load().oracle_asral_order(n, k, _p(cm), _p(cap), _p(pen), 1, int(mode),
+                                        int(max_rounds), int(bool(check)), _p(order), _p(assign),
+                                        _p(load), ctypes.byref(delta), ctypes.byref(st))
     stats = {f: getattr(st, f) for f, _ in _Stats._fields_}
     return Result(assign=assign, load=load, delta=int(delta.value), stats=stats, rc=rc)
+
+
+def insertion_order(cm, n0: int) -> np.ndarray:
+    """Extraction order of a solve of the first n0 units (their MinDistance
+    order) followed by the units n0..n-1 inserted afterwards, in index order
+    (each insertion is one more iteration of Alg. 2)."""
+    cm = _c(cm, np.int32)
+    n = cm.shape[0]
+    if not 1 <= n0 <= n:
+        raise ValueError(f"n0 = {n0} outside [1, {n}]")
+    _, order0 = smin_order(cm[:n0])
+    return np.concatenate([order0, np.arange(n0, n, dtype=np.int32)])
 
 
 def objective_q(cm, cap, qtab, assign) -> int:

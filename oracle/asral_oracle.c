@@ -517,11 +517,18 @@ static void asral_free(asral *S) {
  *         1 = maintained with the paper's BestTransHeaps.
  *   check: if nonzero, after every round verify Lemmas 1/2 (no negative
  *          cycle in Gamma) and the incremental objective against Eq. (1).
+ *   order_in: the extraction order of the units (a permutation of 0..n-1),
+ *          or NULL for the MinDistance order.  Inserting demand units into
+ *          a solved instance (the dynamic update of the paper's proof
+ *          sketch: "identical to one iteration of the loop" of Alg. 2) is
+ *          this loop with the inserted units extracted after all others,
+ *          in insertion order.
  * Outputs assign[n] (-1 = not yet allotted), load[k], *delta, *stats.
  */
-int oracle_asral_q(int64_t n, int64_t k, const int32_t *cm, const int32_t *cap,
-                   const int32_t *qtab, int64_t Q, int mode, int64_t max_rounds, int check,
-                   int32_t *assign, int64_t *load_out, int64_t *delta_out, oracle_stats *stats) {
+int oracle_asral_order(int64_t n, int64_t k, const int32_t *cm, const int32_t *cap,
+                       const int32_t *qtab, int64_t Q, int mode, int64_t max_rounds, int check,
+                       const int32_t *order_in, int32_t *assign, int64_t *load_out,
+                       int64_t *delta_out, oracle_stats *stats) {
     if (n < 1 || k < 1 || Q < 1 || !cm || !cap || !qtab || !assign) return OR_ERR_ARG;
     for (int64_t s = 0; s < k; ++s) {
         if (cap[s] < 1) return OR_ERR_ARG;
@@ -537,6 +544,15 @@ int oracle_asral_q(int64_t n, int64_t k, const int32_t *cm, const int32_t *cap,
     int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     if (rc == OR_OK && (!smin || !order)) rc = OR_ERR_OOM;
     if (rc == OR_OK) rc = oracle_smin_order(n, k, cm, smin, order);
+    if (rc == OR_OK && order_in) {   /* a permutation of the units */
+        char *seen = (char *)calloc((size_t)n, 1);
+        if (!seen) rc = OR_ERR_OOM;
+        for (int64_t r = 0; r < n && rc == OR_OK; ++r) {
+            if (order_in[r] < 0 || order_in[r] >= n || seen[order_in[r]]) rc = OR_ERR_ARG;
+            else { seen[order_in[r]] = 1; order[r] = order_in[r]; }
+        }
+        free(seen);
+    }
     int64_t R = (max_rounds < 0 || max_rounds > n) ? n : max_rounds;
     for (int64_t r = 0; r < R && rc == OR_OK; ++r) {
         int32_t d = order[r];
@@ -565,6 +581,14 @@ int oracle_asral_q(int64_t n, int64_t k, const int32_t *cm, const int32_t *cap,
     free(order);
     asral_free(&S);
     return rc;
+}
+
+/* Alg. 2 in the MinDistance order. */
+int oracle_asral_q(int64_t n, int64_t k, const int32_t *cm, const int32_t *cap,
+                   const int32_t *qtab, int64_t Q, int mode, int64_t max_rounds, int check,
+                   int32_t *assign, int64_t *load_out, int64_t *delta_out, oracle_stats *stats) {
+    return oracle_asral_order(n, k, cm, cap, qtab, Q, mode, max_rounds, check, NULL, assign,
+                              load_out, delta_out, stats);
 }
 
 /* Alg. 2 with the constant per-unit penalty pen[s] of the experiments. */

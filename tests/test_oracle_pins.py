@@ -651,3 +651,87 @@ def test_planted_best_transfer_mistake_is_caught(name, tmp_path):
                                     tc.ctypes.data, td.ctypes.data) == 0
     with pytest.raises(AssertionError):
         _best_transfer_certificate(J.cm, assign, tc, td)
+
+
+# ------------------------------------------- insertion of demand units --
+# The paper's proof sketch of its dynamic-update theorem: adding a demand
+# unit is one more iteration of the loop of Alg. 2.  The oracle runs the loop
+# with the inserted units extracted after the solved ones.
+
+def test_insertion_keeps_the_optimum_after_every_insert():
+    """After the first n0 units are solved and each later unit inserted, the
+    objective is the exact optimum of the units allotted so far (the
+    slot-expanded matching of that sub-instance), the rest are unallotted,
+    and Lemmas 1/2 and Eq. (1) hold after every round."""
+    for s in range(10):
+        n, k = [12, 18, 26][s % 3], [2, 3, 5][s % 3]
+        J = small(3600 + s, n, k, cm_max=[5, 20, 60][s % 3], cap_frac=[0.4, 0.7, 0.9][s % 3],
+                  pen=[(1, 6), (1, 30), (5, 80)][s % 3])
+        n0 = n // 2
+        order = oracle.insertion_order(J.cm, n0)
+        assert np.array_equal(order[n0:], np.arange(n0, n))
+        for m in range(n0, n + 1):
+            r = oracle.asral(J.cm, J.cap, J.pen, order=order, max_rounds=m, check=True)
+            assert r.rc == oracle.OK
+            assert (r.assign[m:] == -1).all() and (r.assign[:m] >= 0).all()
+            assert r.delta == exact.matching_optimum(J.cm[:m], J.cap, J.pen), (s, m)
+
+
+def test_insertion_against_brute_force_on_tiny():
+    for s in range(12):
+        J = small(3700 + s, 8, 3, cm_max=7, cap_frac=0.5, pen=(1, 5))
+        r = oracle.asral(J.cm, J.cap, J.pen, order=oracle.insertion_order(J.cm, 3))
+        assert r.rc == 0 and r.delta == exact.brute_force(J.cm, J.cap, J.pen)
+
+
+def test_units_already_last_in_the_order_insert_like_a_solve():
+    """Inserting units whose (cost, index) keys already come last in the
+    MinDistance order gives exactly the one-shot solve."""
+    J = small(3800, 30, 4, cm_max=9, cap_frac=0.6, pen=(1, 20))
+    _, order = oracle.smin_order(J.cm)
+    last = order[-5:]
+    perm = np.concatenate([np.setdiff1d(np.arange(30), last), last]).astype(np.int32)
+    cm = J.cm[perm]                       # the five units become the last indices
+    ref = oracle.asral(cm, J.cap, J.pen)
+    ins = oracle.asral(cm, J.cap, J.pen, order=oracle.insertion_order(cm, 25))
+    assert ins.delta == ref.delta and np.array_equal(ins.assign, ref.assign)
+
+
+def test_order_must_be_a_permutation():
+    J = small(3900, 10, 3)
+    for bad in ([0] * 10, list(range(1, 11)), [-1] + list(range(1, 10))):
+        assert oracle.asral(J.cm, J.cap, J.pen, order=np.array(bad, np.int32)).rc == oracle.ERR_ARG
+
+
+def test_planted_insertion_mistake_is_caught(tmp_path):
+    """An oracle that ignores the given extraction order fails the
+    per-insert optimum pin."""
+    src = open(_SRC).read()
+    old = "else { seen[order_in[r]] = 1; order[r] = order_in[r]; }"
+    assert src.count(old) == 1
+    mutated = tmp_path / "mut.c"
+    mutated.write_text(src.replace(old, "else { seen[order_in[r]] = 1; }"))
+    so = tmp_path / "mut.so"
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", str(mutated), "-o", str(so)],
+                   check=True)
+    lib = ctypes.CDLL(str(so))
+    P, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.oracle_asral_order.argtypes = [i64, i64, P, P, P, i64, c_int, i64, c_int, P, P, P, P, P]
+    caught = False
+    for s in range(10):
+        J = small(3600 + s, 18, 3, cm_max=20, cap_frac=0.7, pen=(1, 30))
+        order = oracle.insertion_order(J.cm, 9)
+        cm = np.ascontiguousarray(J.cm, np.int32)
+        assign = np.empty(J.n, np.int32)
+        load = np.empty(J.k, np.int64)
+        delta = ctypes.c_int64(0)
+        st = oracle._Stats()
+        rc = lib.oracle_asral_order(J.n, J.k, cm.ctypes.data, J.cap.ctypes.data,
+                                    J.pen.ctypes.data, 1, oracle.MODE_HEAP, 9, 0,
+                                    order.ctypes.data, assign.ctypes.data, load.ctypes.data,
+                                    ctypes.byref(delta), ctypes.byref(st))
+        if rc != 0 or (assign[9:] != -1).any() or \
+                delta.value != exact.matching_optimum(J.cm[:9], J.cap, J.pen):
+            caught = True
+            break
+    assert caught
