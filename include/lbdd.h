@@ -297,6 +297,26 @@ int lbdd_server_get_stats(lbdd_server* srv, lbdd_server_stats* out);
  * waiting in lbdd_server_poll would wait on freed state. */
 void lbdd_server_destroy(lbdd_server* srv);
 
+/* Insert one demand unit into a solver.  The paper's proof sketch of its
+ * dynamic-update theorem (commented out of the text, end of Section 4 and of
+ * the appendix): adding a demand unit is one more iteration of the loop of
+ * Alg. 2 -- allot it to its most suitable center, then Negative Cycle
+ * Refinement and, if that center was full, Negative Path Refinement.
+ *   row      : the unit's k costs (host memory, cm_dtype), every one >= 1; a
+ *              solver that stores its CM as int16 refuses a cost above 32767.
+ *   unit_out : the unit's index, the solver's unit count before the call.
+ * The unit is extracted after every unit already in the solver, in insertion
+ * order: the next lbdd_solve allots it (a solve that has finished runs just
+ * the new rounds).  Before the first round of a solver, inserted units simply
+ * join the instance (the first solve orders all units).  lbdd_reset restarts
+ * a solve of all units in the MinDistance order.  Device arrays grow by half
+ * when full (a short synchronous reallocation).  Errors: LBDD_ERR_ARG (bad
+ * arguments or costs), LBDD_ERR_STATE (a strict-LBDD solver, or one held by a
+ * batch), LBDD_ERR_OOM / LBDD_ERR_CUDA (growth failed; the solver is
+ * unchanged).  Deletion is not provided: the proof sketch leaves the edges of
+ * the reverse path undefined. */
+int lbdd_insert(lbdd_solver* s, const void* row, int cm_dtype, int32_t* unit_out);
+
 /* Tracked objective Delta of Alg. 2 (equals Eq. (1) of the current
  * allotment).  out: host pointer. */
 int lbdd_objective(const lbdd_solver* s, int64_t* out);

@@ -177,20 +177,26 @@ def objective_q(cm, cap, qtab, assign) -> int:
                                           qtab.shape[1], _p(_c(assign, np.int32))))
 
 
-def asral_q(cm, cap, qtab, mode=MODE_HEAP, max_rounds=-1, check=False) -> Result:
-    """Alg. 2 with general penalty functions (Def. 4) given as tables (k x Q)."""
+def asral_q(cm, cap, qtab, mode=MODE_HEAP, max_rounds=-1, check=False, order=None) -> Result:
+    """Alg. 2 with general penalty functions (Def. 4) given as tables (k x Q).
+    order: the units' extraction order (default: the MinDistance order)."""
     cm = _c(cm, np.int32)
     n, k = cm.shape
     cap = _c(cap, np.int32)
     qtab = _c(qtab, np.int32)
     assert qtab.ndim == 2 and qtab.shape[0] == k
+    if order is not None:
+        order = _c(order, np.int32)
+        if order.shape != (n,):
+            raise ValueError(f"order: expected {n} entries, got shape {order.shape}")
     assign = np.empty(n, np.int32)
     load = np.empty(k, np.int64)
     delta = ctypes.c_int64(0)
     st = _Stats()
-    rc = _load().oracle_asral_q(n, k, _p(cm), _p(cap), _p(qtab), qtab.shape[1], int(mode),
-                                int(max_rounds), int(bool(check)), _p(assign), _p(load),
-                                ctypes.byref(delta), ctypes.byref(st))
+    rc = _load().oracle_asral_order(n, k, _p(cm), _p(cap), _p(qtab), qtab.shape[1], int(mode),
+                                    int(max_rounds), int(bool(check)),
+                                    None if order is None else _p(order), _p(assign), _p(load),
+                                    ctypes.byref(delta), ctypes.byref(st))
     stats = {f: getattr(st, f) for f, _ in _Stats._fields_}
     return Result(assign=assign, load=load, delta=int(delta.value), stats=stats, rc=rc)
 

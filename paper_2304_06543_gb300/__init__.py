@@ -19,7 +19,7 @@ import numpy as np
 from . import _build
 
 __all__ = [
-    "load", "LbddError", "Solver", "create", "create_strict", "set_penalty_table", "road_cm", "solve", "reset", "solve_batch", "objective",
+    "load", "LbddError", "Solver", "create", "create_strict", "set_penalty_table", "road_cm", "solve", "reset", "insert", "solve_batch", "objective",
     "assignment", "loads", "rounds_done", "get_stats", "best_transfer_table",
     "best_transfer", "best_transfer_workspace", "cm_pitch", "strerror", "destroy",
     "Batch", "autotune", "tune_get", "tune_clear", "Server", "RequestInfo", "ServerStats",
@@ -91,6 +91,7 @@ def load():
         lib.lbdd_road_cm.argtypes = [i32, P, P, P, i32, P, i32, P, P, i64, P]
         lib.lbdd_solve.argtypes = [P, i64]
         lib.lbdd_reset.argtypes = [P]
+        lib.lbdd_insert.argtypes = [P, P, c_int, ctypes.POINTER(i32)]
         lib.lbdd_solve_batch.argtypes = [ctypes.POINTER(P), c_int, i64, c_int, c_int, P]
         lib.lbdd_objective.argtypes = [P, ctypes.POINTER(i64)]
         lib.lbdd_assignment.argtypes = [P, P, c_int]
@@ -289,6 +290,20 @@ def reset(h):
     _check(load().lbdd_reset(h), "lbdd_reset")
 
 
+def insert(h, row, k: int) -> int:
+    """lbdd_insert: one more demand unit with costs `row` (k entries, int32 or
+    int16); returns its index."""
+    r = np.ascontiguousarray(row)
+    if r.dtype not in (np.int32, np.int16):
+        r = r.astype(np.int32)
+    if r.shape != (int(k),):
+        raise ValueError(f"row: expected {k} entries, got shape {r.shape}")
+    dt = CM_I16 if r.dtype == np.int16 else CM_I32
+    u = ctypes.c_int32()
+    _check(load().lbdd_insert(h, r.ctypes.data, dt, ctypes.byref(u)), "lbdd_insert")
+    return u.value
+
+
 def solve_batch(handles, max_rounds: int = -1, cluster_size: int = 0, max_clusters: int = 0,
                 stream=None):
     arr = _handles(handles)
@@ -420,6 +435,12 @@ class Solver:
     def reset(self):
         reset(self.h)
         return self
+
+    def insert(self, row) -> int:
+        """Append one demand unit (lbdd_insert); returns its index."""
+        u = insert(self.h, row, self.k)
+        self.n += 1
+        return u
 
     @property
     def objective(self) -> int:

@@ -248,6 +248,7 @@ static int create_impl(lbdd_solver** out, int32_t n, int32_t k, const void* cm, 
   lbdd_solver* s = new (std::nothrow) lbdd_solver();
   if (!s) return LBDD_ERR_OOM;
   s->n = n;
+  s->n_cap = n;
   s->k = k;
   s->st = static_cast<cudaStream_t>(cuda_stream);
   int rc = check_device(&s->device, &s->num_sms);
@@ -540,6 +541,148 @@ int lbdd::solve_timed(lbdd_solver* s, int64_t max_rounds, int C, float* ms) {
   CK(cudaStreamSynchronize(s->st));
   CK(cudaEventElapsedTime(ms, ev.a, ev.b));
   return status_to_rc(st);
+}
+
+// ----------------------------------------------------------- insertion ---
+
+// The unit appended as row d (the dynamic update of the paper's proof sketch:
+// adding a demand unit is one more iteration of the loop of Alg. 2): its
+// costs into the CM row (narrowed when the CM is stored as int16; the caller
+// checked the range), its most suitable center (lowest index among the
+// minima), its round at the end of the extraction order, not yet allotted.
+__global__ void insert_unit(void* cm, int elem, int64_t ld, int32_t d, int32_t k,
+                            const int32_t* __restrict__ row, int32_t* smin, int32_t* order,
+                            int32_t* assign, int32_t* pos) {
+  __shared__ int2 part[32];
+  int32_t bv = INT32_MAX, bj = INT32_MAX;
+  for (int32_t c = threadIdx.x; c < k; c += blockDim.x) {
+    const int32_t v = row[c];
+    if (elem == 2) static_cast<int16_t*>(cm)[(int64_t)d * ld + c] = (int16_t)v;
+    else static_cast<int32_t*>(cm)[(int64_t)d * ld + c] = v;
+    if (v < bv) { bv = v; bj = c; }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const int32_t ov = __shfl_xor_sync(0xffffffffu, bv, off);
+    const int32_t oj = __shfl_xor_sync(0xffffffffu, bj, off);
+    if (ov < bv || (ov == bv && oj < bj)) { bv = ov; bj = oj; }
+  }
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = make_int2(bv, bj);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (part[w].x < bv || (part[w].x == bv && part[w].y < bj)) { bv = part[w].x; bj = part[w].y; }
+    smin[d] = bj;
+    order[d] = d;
+    assign[d] = -1;
+    pos[d] = 0;
+  }
+}
+
+// Room for cap_new units: the unit-indexed arrays, the CM rows and the
+// member-list page table and pool are reallocated with their contents; the
+// new pages join the free stack (if no round has run, the prologue builds
+// the stack from all pages anyway).
+static int grow_units(lbdd_solver* s, int32_t cap_new) {
+  const int32_t n = s->n, k = s->k;
+  const int64_t ld = s->ld;
+  const int elem = s->elem;
+  DevInst& I = s->h_inst;
+  const int32_t mp_old = I.max_pages, np_old = I.npages;
+  const int32_t mp_new = (int32_t)(((int64_t)cap_new + kPage - 1) / kPage);
+  const int32_t np_new = mp_new + k;
+  void* cm = nullptr;
+  int32_t *smin = nullptr, *order = nullptr, *sort_tmp = nullptr, *assign = nullptr,
+          *pos = nullptr, *page_tab = nullptr, *pool = nullptr, *free_stack = nullptr;
+  const size_t cm_bytes = ((size_t)cap_new * ld + kColPad) * elem;
+  int rc = dev_alloc(s, &cm, cm_bytes);
+  if (!rc) rc = dalloc(s, &smin, cap_new);
+  if (!rc) rc = dalloc(s, &order, cap_new);
+  if (!rc) rc = dalloc(s, &sort_tmp, 3ull * cap_new);
+  if (!rc) rc = dalloc(s, &assign, cap_new);
+  if (!rc) rc = dalloc(s, &pos, cap_new);
+  if (!rc) rc = dalloc(s, &page_tab, (size_t)k * mp_new);
+  if (!rc) rc = dalloc(s, &pool, (size_t)np_new * kPage);
+  if (!rc) rc = dalloc(s, &free_stack, np_new);
+  if (rc) {   // the solver keeps its old arrays
+    for (void* p : {cm, (void*)smin, (void*)order, (void*)sort_tmp, (void*)assign, (void*)pos,
+                    (void*)page_tab, (void*)pool, (void*)free_stack})
+      if (p) dev_free(s, p);
+    return rc;
+  }
+  const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+  CK(cudaMemsetAsync(cm, 0, cm_bytes, s->st));
+  CK(cudaMemcpyAsync(cm, s->cm, (size_t)n * ld * elem, dd, s->st));
+  CK(cudaMemcpyAsync(smin, s->smin, 4ull * n, dd, s->st));
+  CK(cudaMemcpyAsync(order, s->order, 4ull * n, dd, s->st));
+  CK(cudaMemsetAsync(assign, 0xff, 4ull * cap_new, s->st));
+  CK(cudaMemcpyAsync(assign, s->assign, 4ull * n, dd, s->st));
+  CK(cudaMemsetAsync(pos, 0, 4ull * cap_new, s->st));
+  CK(cudaMemcpyAsync(pos, s->pos, 4ull * n, dd, s->st));
+  CK(cudaMemsetAsync(page_tab, 0, 4ull * k * mp_new, s->st));
+  CK(cudaMemcpy2DAsync(page_tab, 4ull * mp_new, s->page_tab, 4ull * mp_old, 4ull * mp_old, k, dd,
+                       s->st));
+  CK(cudaMemsetAsync(pool, 0, 4ull * np_new * kPage, s->st));
+  CK(cudaMemcpyAsync(pool, s->pool, 4ull * np_old * kPage, dd, s->st));
+  CK(cudaMemcpyAsync(free_stack, s->free_stack, 4ull * np_old, dd, s->st));
+  int64_t h[2];
+  CK(cudaMemcpyAsync(h, s->ctl + CTL_PROLOGUE, sizeof(int64_t), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaMemcpyAsync(h + 1, s->ctl + CTL_FREE_TOP, sizeof(int64_t), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  if (h[0] != 0 && np_new > np_old) {
+    std::vector<int32_t> ids(np_new - np_old);
+    for (int32_t i = 0; i < np_new - np_old; ++i) ids[i] = np_old + i;
+    const int64_t top = h[1] + (int64_t)ids.size();
+    CK(cudaMemcpyAsync(free_stack + h[1], ids.data(), 4ull * ids.size(), cudaMemcpyHostToDevice,
+                       s->st));
+    CK(cudaMemcpyAsync(s->ctl + CTL_FREE_TOP, &top, sizeof(int64_t), cudaMemcpyHostToDevice,
+                       s->st));
+    CK(cudaStreamSynchronize(s->st));
+  }
+  for (void* p : {s->cm, (void*)s->smin, (void*)s->order, (void*)s->sort_tmp, (void*)s->assign,
+                  (void*)s->pos, (void*)s->page_tab, (void*)s->pool, (void*)s->free_stack})
+    dev_free(s, p);
+  s->cm = cm; s->smin = smin; s->order = order; s->sort_tmp = sort_tmp; s->assign = assign;
+  s->pos = pos; s->page_tab = page_tab; s->pool = pool; s->free_stack = free_stack;
+  I.cm = cm; I.smin = smin; I.order = order; I.sort_tmp = sort_tmp; I.assign = assign;
+  I.pos = pos; I.page_tab = page_tab; I.pool = pool; I.free_stack = free_stack;
+  I.max_pages = mp_new;
+  I.npages = np_new;
+  s->n_cap = cap_new;
+  return LBDD_OK;
+}
+
+extern "C" int lbdd_insert(lbdd_solver* s, const void* row, int cm_dtype, int32_t* unit_out) {
+  if (!s || !row || !unit_out) return LBDD_ERR_ARG;
+  if (cm_dtype != LBDD_CM_I32 && cm_dtype != LBDD_CM_I16) return LBDD_ERR_ARG;
+  if (s->strict || s->in_batches > 0) return LBDD_ERR_STATE;
+  if (s->n >= INT32_MAX - 1) return LBDD_ERR_ARG;
+  const int32_t k = s->k;
+  std::vector<int32_t> r(k);
+  for (int32_t c = 0; c < k; ++c) {
+    const int32_t v = cm_dtype == LBDD_CM_I16 ? (int32_t)static_cast<const int16_t*>(row)[c]
+                                              : static_cast<const int32_t*>(row)[c];
+    if (v < 1 || (s->elem == 2 && v > INT16_MAX)) return LBDD_ERR_ARG;
+    r[c] = v;
+  }
+  int rc = LBDD_OK;
+  if (!s->ins_row) rc = dalloc(s, &s->ins_row, k);
+  if (rc) return rc;
+  if (s->n + 1 > s->n_cap) {
+    const int64_t want = (int64_t)s->n_cap + s->n_cap / 2 + 1024;
+    rc = grow_units(s, (int32_t)std::min<int64_t>(want, INT32_MAX - 1));
+    if (rc) return rc;
+  }
+  const int32_t d = s->n;
+  CK(cudaMemcpyAsync(s->ins_row, r.data(), 4ull * k, cudaMemcpyHostToDevice, s->st));
+  insert_unit<<<1, kThreads, 0, s->st>>>(s->cm, s->elem, s->ld, d, k, s->ins_row, s->smin,
+                                         s->order, s->assign, s->pos);
+  CK(cudaGetLastError());
+  s->n = d + 1;
+  s->h_inst.n = s->n;
+  CK(cudaMemcpyAsync(s->d_inst, &s->h_inst, sizeof(DevInst), cudaMemcpyHostToDevice, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  *unit_out = d;
+  return LBDD_OK;
 }
 
 extern "C" int lbdd_reset(lbdd_solver* s) {

@@ -307,6 +307,7 @@ struct lbdd_batch {
 };
 
 static void batch_free(lbdd_batch* b) {
+  for (lbdd_solver* x : b->solvers) x->in_batches--;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->st) cudaStreamSynchronize(b->st);
@@ -398,7 +399,9 @@ int batch_set(lbdd_batch* b, lbdd_solver* const* solvers, const int64_t* rem, in
     if (!solvers[i] || solvers[i]->device != b->dev) return LBDD_ERR_ARG;
     r[i] = rem ? std::max<int64_t>(rem[i], 1) : solvers[i]->n;
   }
+  for (lbdd_solver* old : b->solvers) old->in_batches--;
   b->solvers.assign(solvers, solvers + m);
+  for (lbdd_solver* x : b->solvers) x->in_batches++;
   int rc = make_plan(solvers, r.data(), m, cluster_size, max_clusters, b->dev, b->sms,
                      shortest_first ? SHORTEST_FIRST : LONGEST_FIRST, first, &b->groups,
                      &b->cluster_of);

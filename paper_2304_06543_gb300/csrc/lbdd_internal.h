@@ -53,6 +53,9 @@ struct lbdd_solver {
   int strict = 0;          // strict-LBDD instance (Alg. 5), k includes a dummy center if any
   int device = 0;
   int num_sms = 0;
+  int32_t n_cap = 0;       // units the unit-indexed arrays and the page pool hold (>= n)
+  int in_batches = 0;      // batches that hold a copy of this solver's device view
+  int32_t* ins_row = nullptr;  // k costs of a unit being inserted (device staging)
   size_t bytes = 0;        // device bytes held now
   std::vector<void*> allocs;
   std::vector<size_t> sizes;

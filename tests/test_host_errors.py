@@ -107,6 +107,8 @@ def test_null_handles_are_rejected(lb, lib):
     buf = np.zeros(16, np.int32)
     assert lib.lbdd_solve(None, -1) == lb.ERR_ARG
     assert lib.lbdd_reset(None) == lb.ERR_ARG
+    u = ctypes.c_int32()
+    assert lib.lbdd_insert(None, _ptr(buf), lb.CM_I32, ctypes.byref(u)) == lb.ERR_ARG
     assert lib.lbdd_set_option(None, lb.OPT_CLUSTER, 1) == lb.ERR_ARG
     assert lib.lbdd_set_penalty_table(None, _ptr(buf), 1) == lb.ERR_ARG
     assert lib.lbdd_objective(None, ctypes.byref(i64)) == lb.ERR_ARG
