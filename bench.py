@@ -1014,40 +1014,53 @@ def batch_measure(lb, rank: int, world: int, m: int = 256, seq_every: int = 8,
                         "[10, 400), one CUDA-graph replay"}
 
 
-def scan_measure(lb, hbm_peak, peak_kind, reps: int = 20):
-    """Full best-transfer table (lbdd_best_transfer) of the s_min allotment of
-    the 2,000,000 x 2,000 instance, int16 (8 GB) and int32 (16 GB); bytes =
-    n*k*w + 4n per call; 20 timed calls after 3 warm-ups (inputs > L2)."""
+def _scan_case(lb, cm_host, dt, hbm_peak, peak_kind, reps):
+    """Whole-call device time of lbdd_best_transfer on the s_min allotment of
+    `cm_host` stored as `dt`; bytes = n*k*w + 4n per call."""
     import torch
+    n, k = cm_host.shape
+    cmd = lb.CM_I16 if dt == "i16" else lb.CM_I32
+    ld = lb.cm_pitch(k, cmd)
+    tdt = torch.int16 if dt == "i16" else torch.int32
+    buf = torch.zeros(n * ld + 128, dtype=tdt, device="cuda")
+    view = buf[: n * ld].view(n, ld)
+    chunk = max(1, (1 << 28) // k)
+    for a in range(0, n, chunk):
+        b = min(a + chunk, n)
+        view[a:b, :k].copy_(torch.from_numpy(cm_host[a:b]).cuda().to(tdt))
+    assign = torch.argmin(view[:, :k], dim=1).to(torch.int32)
+    ms, tc, td = _scan_gbs(lb, buf, cmd, ld, n, k, assign, reps)
+    w = 2 if dt == "i16" else 4
+    byts = n * k * w + 4 * n
+    gbs = byts / ms / 1e6
+    out = {"kernel": "lbdd_best_transfer (all stages)", "bound": "hbm", "achieved": gbs,
+           "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak, "peak_kind": peak_kind,
+           "traffic": None, "ms": ms, "bytes": byts,
+           "table_sha256": hashlib.sha256(tc.cpu().numpy().tobytes() +
+                                          td.cpu().numpy().tobytes()).hexdigest()}
+    del buf, view, assign, tc, td
+    torch.cuda.empty_cache()
+    return out
+
+
+def scan_measure(lb, hbm_peak, peak_kind, reps: int = 20):
+    """Full best-transfer table (lbdd_best_transfer) of the s_min allotment:
+    the 2,000,000 x 2,000 instance, int16 (8 GB) and int32 (16 GB), and the
+    200,000 x 500 city instance, int16 (200 MB) and int32 (400 MB); 20 timed
+    calls after 3 warm-ups, inputs larger than L2."""
     import lbdd_inputs as L
     inst = L.make_named("large", dtype="i16")
-    n, k = inst.n, inst.k
-    out = {}
-    for dt in ("i16", "i32"):
-        cmd = lb.CM_I16 if dt == "i16" else lb.CM_I32
-        ld = lb.cm_pitch(k, cmd)
-        tdt = torch.int16 if dt == "i16" else torch.int32
-        buf = torch.zeros(n * ld + 128, dtype=tdt, device="cuda")
-        src = torch.from_numpy(inst.cm.reshape(-1))
-        chunk = 1 << 28
-        for a in range(0, n * k, chunk):
-            b = min(a + chunk, n * k)
-            buf[a:b].copy_(src[a:b].cuda().to(tdt))
-        assign = torch.argmin(buf[: n * k].view(n, k), dim=1).to(torch.int32)
-        ms, tc, td = _scan_gbs(lb, buf, cmd, ld, n, k, assign, reps)
-        w = 2 if dt == "i16" else 4
-        byts = n * k * w + 4 * n
-        gbs = byts / ms / 1e6
-        out[dt] = {"kernel": "lbdd_best_transfer (all stages)", "bound": "hbm", "achieved": gbs,
-                   "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                   "peak_kind": peak_kind, "traffic": None, "ms": ms, "bytes": byts,
-                   "table_sha256": hashlib.sha256(tc.cpu().numpy().tobytes() +
-                                                  td.cpu().numpy().tobytes()).hexdigest()}
-        del buf, assign, tc, td
-        torch.cuda.empty_cache()
+    out = {dt: _scan_case(lb, inst.cm, dt, hbm_peak, peak_kind, reps) for dt in ("i16", "i32")}
     out["tables_equal_i16_i32"] = out["i16"]["table_sha256"] == out["i32"]["table_sha256"]
     out["workload"] = ("s_min allotment of the 2,000,000 x 2,000 instance (clustered demand, "
                        "road factors); CM 8 GB int16 / 16 GB int32, larger than L2")
+    del inst
+    city = L.make_named("city", dtype="i16")
+    c = {dt: _scan_case(lb, city.cm, dt, hbm_peak, peak_kind, reps) for dt in ("i16", "i32")}
+    c["tables_equal_i16_i32"] = c["i16"]["table_sha256"] == c["i32"]["table_sha256"]
+    c["workload"] = ("s_min allotment of the 200,000 x 500 city instance; CM 200 MB int16 / "
+                     "400 MB int32, larger than L2")
+    out["city"] = c
     return out
 
 

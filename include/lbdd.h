@@ -368,7 +368,9 @@ const char* lbdd_last_cuda_error(void);
  *   stream     : cudaStream_t or NULL.  Asynchronous: results are ready
  *                when the stream reaches this point.
  * Errors: LBDD_ERR_ARG (sizes, alignment, workspace too small),
- * LBDD_ERR_CUDA (launch failure). */
+ * LBDD_ERR_CUDA (launch failure).  Every wait inside the scan is bounded
+ * (1 s); one that runs out marks the whole table (tc = INT32_MAX, td = -2)
+ * instead of returning a partial result. */
 size_t lbdd_best_transfer_workspace(int32_t n, int32_t k);
 int lbdd_best_transfer(int32_t n, int32_t k, const void* cm_dev, int cm_dtype, int64_t ld,
                        const int32_t* assign_dev, int32_t* tc_dev, int32_t* td_dev,
@@ -385,7 +387,7 @@ int lbdd_best_transfer(int32_t n, int32_t k, const void* cm_dev, int cm_dtype, i
  *   caller's device buffers), without the workspace.
  *   Limit: lbdd_best_transfer_workspace(n, k) must not exceed 64 MiB, else
  *   LBDD_ERR_BUDGET is returned and nothing is launched (the city-scale
- *   200,000 x 500 case needs 6,072,320 bytes, about 5.8 MiB).
+ *   200,000 x 500 case needs 2,988,800 bytes, about 2.9 MiB).
  *   The first call on each device looks up the device address of the array
  *   (with that device current); make that first call before any stream
  *   capture.

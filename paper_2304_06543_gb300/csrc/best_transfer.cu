@@ -6,18 +6,29 @@
 //   T[u][v] = lexmin over d with assign[d] == u of (CM(d,v) - CM(d,u), d)
 //
 // Pipeline (all device-side, one stream):
-//   1. stable LSD radix sort of (assign[d], d) -> units grouped by center,
-//      ascending d inside each center (grid-wide, 8-bit digits);
-//   2. segment bounds and a list of work items, each at most kChunk rows of
-//      one center;
-//   3. the scan: each CTA streams its item's CM rows with 16-byte loads,
-//      every thread keeps a running minimum for 16 bytes' worth of columns;
-//      rows arrive in increasing d, so a strict '<' already keeps the lowest
-//      d on equal cost; the partial minima of the CTA are combined in shared
-//      memory and merged into a packed (cost, d) 64-bit table with atomicMin;
-//   4. unpack to the (tc, td) int32 pair.
-// Step 3 reads every CM byte of the allotted rows exactly once and is the
-// HBM-bound kernel; everything else moves O(n + k*k) bytes.
+//   1. bt_count: units per center.  kTiles CTAs, each a contiguous range of
+//      units, count in shared memory; one returned atomic per (tile, center)
+//      adds the tile's count to the center's total and gives the tile its
+//      block inside the center's segment;
+//   2. bt_plan (one CTA): segment offsets from the totals, and work items of
+//      at most `chunk` rows of one center, `chunk` chosen so that every SM
+//      gets about kItemsPerSm items;
+//   3. bt_place: each tile writes its units into its blocks (shared-memory
+//      cursors; the order inside a block is arbitrary);
+//   4. bt_sort_items: the unit ids of every item in ascending order (bitonic:
+//      shuffles below a stride of 32, shared memory above), so that inside
+//      an item a lower row index is a lower d; the packed table is set to its
+//      identity in the same launch;
+//   5. the scan: CM rows are streamed and every 16-byte column group keeps a
+//      running lexicographic minimum; at the end of an item (or of a CTA's
+//      share of one) the partial minima are folded in shared memory and
+//      merged into a packed (cost, d) 64-bit table with atomicMin.  Rows of
+//      512 bytes and more: bt_scan_bulk, every CTA an equal contiguous share
+//      of the grouped rows, staged whole by bulk copies; shorter rows:
+//      bt_scan_rows, items from a queue, 16 bytes per thread and load;
+//   6. bt_unpack: the (tc, td) int32 pair.
+// Step 5 reads every CM byte of the allotted rows once and is the HBM-bound
+// kernel; the other steps move O(n + k*k) bytes.
 #include <atomic>
 #include <algorithm>
 
@@ -25,22 +36,24 @@
 
 namespace lbdd {
 
-constexpr int kTile = kThreads * 8;     // radix-sort tile (elements)
-constexpr int kChunk = 512;             // rows per scan work item
-constexpr int kScanUnroll = 6;          // rows in flight per thread (plus ids of the next 6)
+constexpr int kChunkMax = 512;          // rows per work item, at most (16-bit row index)
+constexpr int kChunkMin = 64;           // rows per work item, at least (bounds the item count)
+constexpr int kItemsPerSm = 8;          // work items per SM the plan aims for
+constexpr int kScanUnroll = 6;          // bt_scan_rows: rows in flight per thread
+constexpr int kTiles = 64;              // unit ranges of bt_count / bt_place
+constexpr int kTileThreads = 1024;
+constexpr int kTileUnroll = 8;          // assign loads in flight per thread
+
+// ctl words (int32): error flag, scan queue, item count, chunk, allotted rows
+enum { BT_ERR = 0, BT_QUEUE, BT_ITEMS, BT_CHUNK, BT_ROWS, BT_CTL_WORDS = 8 };
 
 struct BtWorkspace {
-  int32_t *k0, *v0, *k1, *v1;   // radix ping-pong
-  int32_t* tile_hist;           // 256 x ntiles
-  int32_t* seg_start;           // k
-  int32_t* seg_end;             // k
-  int32_t* item_off;            // k + 1
-  unsigned long long* t64;      // k x k packed (cost + 2^31) << 32 | d
-  int4* items;                  // explicit work items {center, first row, rows, 0}
-  int* err;                     // [0] unused, [1] the work-item queue counter
-  int32_t* dsum;                // 256 digit totals of a radix pass
-  int32_t* ownv;                // n: CM(d, center of d) in sorted order (int16 scan)
-  int64_t ntiles;
+  int* ctl;                     // BT_CTL_WORDS control words
+  int32_t* cnt;                 // k + 1: units per center, then segment starts (cnt[k] = rows)
+  int32_t* tile_rel;            // kTiles x k: a tile's block offset inside a center's segment
+  int32_t* perm;                // n (+ 4 readable): allotted units grouped by center
+  int4* items;                  // n / kChunkMin + k + 1 items {center, first row, rows, 0}
+  unsigned long long* t64;      // k x k packed ((cost + 2^31) << 32) | d
   size_t bytes;
 };
 
@@ -48,26 +61,19 @@ static inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static BtWorkspace carve(void* base, int32_t n, int32_t k) {
   BtWorkspace W;
-  W.ntiles = (n + kTile - 1) / kTile;
   size_t o = 0;
   auto take = [&](size_t bytes) {
     char* p = static_cast<char*>(base) + o;
     o = al256(o + bytes);
     return p;
   };
-  W.k0 = reinterpret_cast<int32_t*>(take(4ull * n));
-  W.v0 = reinterpret_cast<int32_t*>(take(4ull * n));
-  W.k1 = reinterpret_cast<int32_t*>(take(4ull * n));
-  W.v1 = reinterpret_cast<int32_t*>(take(4ull * n));
-  W.tile_hist = reinterpret_cast<int32_t*>(take(4ull * 256 * W.ntiles));
-  W.seg_start = reinterpret_cast<int32_t*>(take(4ull * k));
-  W.seg_end = reinterpret_cast<int32_t*>(take(4ull * k));
-  W.item_off = reinterpret_cast<int32_t*>(take(4ull * (k + 1)));
+  // ctl then cnt: one memset clears both
+  W.ctl = reinterpret_cast<int*>(take(4 * BT_CTL_WORDS + 4ull * (k + 1)));
+  W.cnt = W.ctl + BT_CTL_WORDS;
+  W.tile_rel = reinterpret_cast<int32_t*>(take(4ull * kTiles * k));
+  W.perm = reinterpret_cast<int32_t*>(take(4ull * n + 16));   // id windows round up to 16 bytes
+  W.items = reinterpret_cast<int4*>(take(16ull * ((size_t)n / kChunkMin + (size_t)k + 1)));
   W.t64 = reinterpret_cast<unsigned long long*>(take(8ull * k * k));
-  W.items = reinterpret_cast<int4*>(take(16ull * ((size_t)n / kChunk + (size_t)k + 1)));
-  W.err = reinterpret_cast<int*>(take(16));   // err, then the item queue counter
-  W.dsum = reinterpret_cast<int32_t*>(take(4 * 256));
-  W.ownv = reinterpret_cast<int32_t*>(take(4ull * n));
   W.bytes = o;
   return W;
 }
@@ -77,52 +83,40 @@ size_t bt_workspace_bytes(int32_t n, int32_t k) {
   return carve(nullptr, n, k).bytes + 256;
 }
 
-// ------------------------------------------------------------ radix sort ---
+// ------------------------------------------------------------- grouping ---
 
-// keys = assign (unallotted units -> bucket k, sorted last); values = d.
-__global__ void __launch_bounds__(kThreads) bt_init_keys(const int32_t* __restrict__ assign,
-                                                         int32_t n, int32_t k, int32_t* keys,
-                                                         int32_t* vals) {
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * kThreads) {
-    int32_t a = assign[i];
-    keys[i] = (a < 0 || a >= k) ? k : a;
-    vals[i] = (int32_t)i;
-  }
+// Units of this CTA's tile: [t * per, min(n, (t + 1) * per)).
+__device__ __forceinline__ void tile_range(int32_t n, int64_t* lo, int64_t* hi) {
+  const int64_t per = ((int64_t)n + kTiles - 1) / kTiles;
+  *lo = min((int64_t)n, (int64_t)blockIdx.x * per);
+  *hi = min((int64_t)n, *lo + per);
 }
 
-__global__ void __launch_bounds__(kThreads) bt_hist(const int32_t* __restrict__ keys, int32_t n,
-                                                    int shift, int32_t* tile_hist,
-                                                    int64_t ntiles) {
-  __shared__ int32_t h[256];
-  for (int i = threadIdx.x; i < 256; i += kThreads) h[i] = 0;
+// Units per center and per (tile, center).  Entries of assign outside
+// [0, k) are not counted.
+__global__ void __launch_bounds__(kTileThreads) bt_count(const int32_t* __restrict__ assign,
+                                                         int32_t n, int32_t k, int32_t* cnt,
+                                                         int32_t* tile_rel) {
+  extern __shared__ int32_t h[];   // k counters
+  const int tid = threadIdx.x;
+  for (int i = tid; i < k; i += kTileThreads) h[i] = 0;
   __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * kTile;
-  for (int i = threadIdx.x; i < kTile; i += kThreads) {
-    const int64_t g = base + i;
-    if (g < n) atomicAdd(&h[(keys[g] >> shift) & 255], 1);
+  int64_t lo, hi;
+  tile_range(n, &lo, &hi);
+  for (int64_t b = lo; b < hi; b += (int64_t)kTileThreads * kTileUnroll) {
+    int32_t a[kTileUnroll];
+#pragma unroll
+    for (int u = 0; u < kTileUnroll; ++u) {
+      const int64_t i = b + u * kTileThreads + tid;
+      a[u] = i < hi ? assign[i] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < kTileUnroll; ++u)
+      if (a[u] >= 0 && a[u] < k) atomicAdd(&h[a[u]], 1);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 256; i += kThreads) tile_hist[(int64_t)i * ntiles + blockIdx.x] = h[i];
-}
-
-// Exclusive scan of a device array of length m, one CTA.
-__global__ void __launch_bounds__(kThreads) bt_scan(int32_t* a, int64_t m, int32_t* total_out) {
-  __shared__ int32_t part[kThreads];
-  const int64_t per = (m + kThreads - 1) / kThreads;
-  const int64_t lo = threadIdx.x * per, hi = min(m, lo + per);
-  int32_t s = 0;
-  for (int64_t i = lo; i < hi; ++i) s += a[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int32_t run = 0;
-    for (int t = 0; t < kThreads; ++t) { int32_t c = part[t]; part[t] = run; run += c; }
-    if (total_out) *total_out = run;
-  }
-  __syncthreads();
-  int32_t run = part[threadIdx.x];
-  for (int64_t i = lo; i < hi; ++i) { int32_t c = a[i]; a[i] = run; run += c; }
+  for (int i = tid; i < k; i += kTileThreads)
+    if (h[i]) tile_rel[(int64_t)blockIdx.x * k + i] = atomicAdd(&cnt[i], h[i]);
 }
 
 // Block-wide exclusive scan of one value per thread; returns this thread's
@@ -153,145 +147,128 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* s_wa
   return before + x - v;
 }
 
-// Digit totals of a radix pass: CTA d sums row d of the digit-major
-// histogram (one row per digit, one column per tile).
-__global__ void __launch_bounds__(kThreads) bt_digit_sums(const int32_t* __restrict__ tile_hist,
-                                                          int64_t ntiles, int32_t* dsum) {
+// One CTA of kThreads: segment starts (exclusive prefix of the counts,
+// centers in index order) into cnt[0..k), the allotted total into cnt[k],
+// and the work items.  Clears the scan queue; records the item count, the
+// chunk and the allotted rows in ctl.
+__global__ void __launch_bounds__(kThreads) bt_plan(int32_t* cnt, int32_t k, int num_sms,
+                                                    int4* items, int* ctl) {
   __shared__ int32_t s_warp[kWarps];
-  const int32_t* row = tile_hist + (int64_t)blockIdx.x * ntiles;
-  int32_t s = 0;
-  for (int64_t i = threadIdx.x; i < ntiles; i += kThreads) s += row[i];
+  const int tid = threadIdx.x;
+  const int per = (k + kThreads - 1) / kThreads;
+  const int c0 = min(k, tid * per), c1 = min(k, c0 + per);
+  int32_t rows = 0;
+  for (int c = c0; c < c1; ++c) rows += cnt[c];
   int32_t total;
-  block_exclusive_scan(s, s_warp, &total);
-  if (threadIdx.x == 0) dsum[blockIdx.x] = total;
+  int32_t r = block_exclusive_scan(rows, s_warp, &total);
+  const int64_t want = (int64_t)num_sms * kItemsPerSm;
+  const int64_t even = ((int64_t)total + want - 1) / want;
+  const int32_t chunk = (int32_t)(even < kChunkMin ? kChunkMin : even > kChunkMax ? kChunkMax : even);
+  int32_t its = 0;
+  for (int c = c0; c < c1; ++c) its += (cnt[c] + chunk - 1) / chunk;
+  __syncthreads();                       // s_warp is reused
+  int32_t nitems;
+  int32_t it = block_exclusive_scan(its, s_warp, &nitems);
+  for (int c = c0; c < c1; ++c) {
+    const int32_t m = cnt[c];
+    for (int32_t j = 0; j < m; j += chunk) items[it++] = make_int4(c, r + j, min(chunk, m - j), 0);
+    cnt[c] = r;
+    r += m;
+  }
+  if (tid == 0) {
+    cnt[k] = total;
+    ctl[BT_QUEUE] = 0;
+    ctl[BT_ITEMS] = nitems;
+    ctl[BT_CHUNK] = chunk;
+    ctl[BT_ROWS] = total;
+  }
 }
 
-// Exclusive scan of the whole digit-major histogram, one CTA per digit row:
-// the row's base is the sum of the lower digits' totals, then the row is
-// scanned in contiguous per-thread chunks.
-__global__ void __launch_bounds__(kThreads) bt_digit_scan(int32_t* tile_hist, int64_t ntiles,
-                                                          const int32_t* __restrict__ dsum) {
-  __shared__ int32_t s_warp[kWarps];
-  __shared__ int32_t s_base;
-  const int d = blockIdx.x;
-  int32_t b = threadIdx.x < d ? dsum[threadIdx.x] : 0;   // d <= 255 < kThreads
-  int32_t btot;
-  block_exclusive_scan(b, s_warp, &btot);
-  if (threadIdx.x == 0) s_base = btot;
+// Each tile's units into its blocks: cursor of center c = segment start +
+// the tile's offset, advanced by shared-memory atomics.
+__global__ void __launch_bounds__(kTileThreads) bt_place(const int32_t* __restrict__ assign,
+                                                         int32_t n, int32_t k,
+                                                         const int32_t* __restrict__ seg,
+                                                         const int32_t* __restrict__ tile_rel,
+                                                         int32_t* perm) {
+  extern __shared__ int32_t cur[];   // k cursors (entries of centers absent from the tile unused)
+  const int tid = threadIdx.x;
+  for (int i = tid; i < k; i += kTileThreads)
+    cur[i] = (int32_t)((uint32_t)seg[i] + (uint32_t)tile_rel[(int64_t)blockIdx.x * k + i]);
   __syncthreads();
-  const int32_t base = s_base;
-  int32_t* row = tile_hist + (int64_t)d * ntiles;
-  const int64_t per = (ntiles + kThreads - 1) / kThreads;
-  const int64_t lo = min(ntiles, (int64_t)threadIdx.x * per), hi = min(ntiles, lo + per);
-  int32_t s = 0;
-  for (int64_t i = lo; i < hi; ++i) s += row[i];
-  int32_t total;
-  __syncthreads();                     // s_warp is reused
-  int32_t run = base + block_exclusive_scan(s, s_warp, &total);
-  for (int64_t i = lo; i < hi; ++i) {
-    const int32_t c = row[i];
-    row[i] = run;
-    run += c;
-  }
-}
-
-// Stable scatter of one tile, in order, 512 elements at a time.
-__global__ void __launch_bounds__(kThreads) bt_scatter(const int32_t* __restrict__ sk,
-                                                       const int32_t* __restrict__ sv,
-                                                       int32_t* dk, int32_t* dv, int32_t n,
-                                                       int shift,
-                                                       const int32_t* __restrict__ tile_hist,
-                                                       int64_t ntiles) {
-  __shared__ int32_t s_off[256];
-  __shared__ int32_t s_wc[kWarps * 256];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint32_t lt;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-  for (int i = tid; i < 256; i += kThreads) s_off[i] = tile_hist[(int64_t)i * ntiles + blockIdx.x];
-  const int64_t base = (int64_t)blockIdx.x * kTile;
-  for (int c = 0; c < kTile; c += kThreads) {
-    const int64_t i = base + c + tid;
-    const bool valid = i < n;
-    const int32_t key = valid ? sk[i] : 0, val = valid ? sv[i] : 0;
-    const int dig = valid ? ((key >> shift) & 255) : 256;
-    const uint32_t peers = __match_any_sync(0xffffffffu, dig);
-    const int rk = __popc(peers & lt);
-    const bool leader = (__ffs(peers) - 1) == lane;
-    for (int x = tid; x < kWarps * 256; x += kThreads) s_wc[x] = 0;
-    __syncthreads();
-    if (valid && leader) s_wc[warp * 256 + dig] = __popc(peers);
-    __syncthreads();
-    if (tid < 256) {
-      int32_t run = s_off[tid];
-      for (int ww = 0; ww < kWarps; ++ww) {
-        const int32_t cnt = s_wc[ww * 256 + tid];
-        s_wc[ww * 256 + tid] = run;
-        run += cnt;
-      }
-      s_off[tid] = run;
+  int64_t lo, hi;
+  tile_range(n, &lo, &hi);
+  for (int64_t b = lo; b < hi; b += (int64_t)kTileThreads * kTileUnroll) {
+    int32_t a[kTileUnroll];
+#pragma unroll
+    for (int u = 0; u < kTileUnroll; ++u) {
+      const int64_t i = b + u * kTileThreads + tid;
+      a[u] = i < hi ? assign[i] : -1;
     }
-    __syncthreads();
-    if (valid) {
-      const int32_t at = s_wc[warp * 256 + dig] + rk;
-      dk[at] = key;
-      dv[at] = val;
-    }
-    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kTileUnroll; ++u)
+      if (a[u] >= 0 && a[u] < k)
+        perm[atomicAdd(&cur[a[u]], 1)] = (int32_t)(b + u * kTileThreads + tid);
   }
 }
 
-// Segment bounds of the sorted keys; with cm16, also the own cost
-// CM(d, c) of every sorted unit (for the staged int16 scan).
-__global__ void __launch_bounds__(kThreads) bt_bounds(const int32_t* __restrict__ keys,
-                                                      const int32_t* __restrict__ vals,
-                                                      int32_t n, int32_t k, int32_t* seg_start,
-                                                      int32_t* seg_end,
-                                                      const int16_t* __restrict__ cm16, int64_t ld,
-                                                      int32_t* ownv) {
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * kThreads) {
-    const int32_t c = keys[i];
-    if (c >= k) continue;
-    if (i == 0 || keys[i - 1] != c) seg_start[c] = (int32_t)i;
-    if (i == n - 1 || keys[i + 1] != c) seg_end[c] = (int32_t)i + 1;
-    if (cm16) ownv[i] = cm16[(int64_t)vals[i] * ld + c];
-  }
-}
-
-__global__ void __launch_bounds__(kThreads) bt_items(const int32_t* __restrict__ seg_start,
-                                                     const int32_t* __restrict__ seg_end,
-                                                     int32_t k, int32_t* item_cnt,
-                                                     unsigned long long* t64) {
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < k;
-       i += (int64_t)gridDim.x * kThreads) {
-    const int32_t s = seg_end[i] - seg_start[i];
-    item_cnt[i] = (s + kChunk - 1) / kChunk;
-  }
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < (int64_t)k * k;
+// The unit ids of each item in ascending order, one item per CTA at a time:
+// thread i holds element i; compare-exchange partners at a stride below 32
+// are reached by shuffles, the others through a double-buffered shared
+// array (one barrier per step).  Also sets the packed table to ~0.
+__global__ void __launch_bounds__(kThreads) bt_sort_items(const int4* __restrict__ items,
+                                                          const int* __restrict__ ctl,
+                                                          int32_t* perm, int32_t k,
+                                                          unsigned long long* t64) {
+  __shared__ int32_t xs[2][kChunkMax];
+  const int tid = threadIdx.x;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + tid; i < (int64_t)k * k;
        i += (int64_t)gridDim.x * kThreads)
     t64[i] = ~0ull;
-}
-
-// Explicit item list: item_off[c] + i -> {c, first row, rows}.
-__global__ void __launch_bounds__(kThreads) bt_item_list(const int32_t* __restrict__ seg_start,
-                                                         const int32_t* __restrict__ seg_end,
-                                                         const int32_t* __restrict__ item_off,
-                                                         int32_t k, int4* items) {
-  for (int64_t c = blockIdx.x * (int64_t)kThreads + threadIdx.x; c < k;
-       c += (int64_t)gridDim.x * kThreads) {
-    const int32_t s0 = seg_start[c], s1 = seg_end[c];
-    int32_t it = item_off[c];
-    for (int32_t r = s0; r < s1; r += kChunk, ++it) items[it] = make_int4((int)c, r, min(kChunk, s1 - r), 0);
+  const int total = ctl[BT_ITEMS];
+  int buf = 0;     // kept across items: consecutive shared steps alternate buffers
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    const int4 desc = items[it];
+    const int32_t r0 = desc.y, m = desc.z;
+    if (m <= 1) continue;
+    int P = 2;
+    while (P < m) P <<= 1;
+    int32_t v = tid < m ? perm[r0 + tid] : INT32_MAX;
+    for (int size = 2; size <= P; size <<= 1) {
+      const bool up = (tid & size) == 0;
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        int32_t w;
+        if (stride >= 32) {
+          xs[buf][tid] = v;
+          __syncthreads();
+          w = xs[buf][tid ^ stride];
+          buf ^= 1;
+        } else {
+          w = __shfl_xor_sync(0xffffffffu, v, stride);
+        }
+        v = (((tid & stride) == 0) == up) ? min(v, w) : max(v, w);
+      }
+    }
+    if (tid < m) perm[r0 + tid] = v;
   }
 }
 
 // ------------------------------------------------------------------ scan ---
+//
+// Keys of the int16 scan: one 32-bit key per column, ((t + 32768) << 16) |
+// row of the item, so the lexicographic (t, d) minimum is one unsigned min
+// (rows of an item are in increasing d; t fits 16 bits because costs are
+// positive int16).  The int32 scan keeps (t, row) pairs with a strict '<':
+// a thread sees the rows of an item in increasing order.
 
+// Rows shorter than 512 bytes: every thread loads its 16-byte column group
+// of kScanUnroll rows at once, and the unit ids of the next kScanUnroll rows
+// while those are reduced.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1)
 bt_scan_rows(const T* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
-             const int32_t* __restrict__ perm, const int32_t* __restrict__ item_off,
-             const int4* __restrict__ items, unsigned long long* t64, int* work) {
+             const int32_t* __restrict__ perm, const int4* __restrict__ items,
+             unsigned long long* t64, int* ctl) {
   constexpr int VPL = 16 / (int)sizeof(T);
   constexpr int U = kScanUnroll;
   __shared__ int2 red[kThreads * VPL];
@@ -299,7 +276,8 @@ bt_scan_rows(const T* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
   const int S = (k + VPL - 1) / VPL;       // 16-byte column groups per row
   const int R = kThreads / S;              // row groups
   const int tid = threadIdx.x, slot = tid % S, g = tid / S;
-  const int32_t total = item_off[k];
+  const int32_t total = ctl[BT_ITEMS];
+  int* work = ctl + BT_QUEUE;
   // items come from a global queue: CTAs that finish early take more
   if (tid == 0) s_item[0] = atomicAdd(work, 1);
   __syncthreads();
@@ -312,17 +290,10 @@ bt_scan_rows(const T* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
     int32_t bt[VPL], bd[VPL];
 #pragma unroll
     for (int q = 0; q < VPL; ++q) { bt[q] = kTInf; bd[q] = -1; }
-    // int16 costs: one 32-bit key per column, ((t + 32768) << 16) | row of
-    // the item, so the lexicographic (t, d) minimum is one unsigned min
-    // (rows of an item are in increasing d; t fits 16 bits because costs
-    // are positive int16)
     uint32_t key[VPL];
 #pragma unroll
     for (int q = 0; q < VPL; ++q) key[q] = 0xffffffffu;
     if (g < R) {
-      // software pipeline: the unit ids of the next U rows are loaded while
-      // the current U rows are loaded and reduced.  Rows of a thread arrive
-      // in increasing d, so a strict '<' keeps the lowest d on equal cost.
       int32_t dn[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -394,9 +365,9 @@ bt_scan_rows(const T* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
         if (lex_less(e.x, e.y, t, dd)) { t = e.x; dd = e.y; }
       }
       if (dd >= 0 && col != c) {
-        const unsigned long long key =
+        const unsigned long long pk =
             ((unsigned long long)(uint32_t)(t + (int64_t)2147483648LL) << 32) | (uint32_t)dd;
-        atomicMin(&t64[(int64_t)c * k + col], key);
+        atomicMin(&t64[(int64_t)c * k + col], pk);
       }
     }
     item = s_item[1];
@@ -405,131 +376,322 @@ bt_scan_rows(const T* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
   }
 }
 
-// ------------------------------------------------ staged int16 row scan ---
+
+// ---------------------------------------------------- bulk-copy row scan ---
 //
-// The int16 scan of the rows of an item, with each thread's 16-byte chunk of
-// a row copied global -> shared by cp.async kStages rows ahead: the bytes in
-// flight are bounded by shared memory, not by registers.  A thread waits only
-// for its own copies (cp.async.wait_group), so no barrier is involved.  Unit
-// ids and own costs (CM(d, c), gathered in sorted order by bt_bounds) travel
-// in register rings two and one stages ahead.  Keys as in bt_scan_rows.
-constexpr int kStages = 10;
+// Rows of kBulkMinRowBytes and more.  CTA b scans the grouped rows
+// [b * rows / G, (b + 1) * rows / G) of perm: equal bytes per CTA, no work
+// queue.  Warp kWarps (the producer) walks that range: the segment starts
+// (all k + 1 of them, copied into shared memory at start) give the center
+// and the item boundaries of every position, the unit ids arrive in windows
+// of kIdsWin by bulk copy one window ahead, and every CM row is copied whole
+// global -> shared by one bulk copy (cp.async.bulk) into a ring of NS stages
+// of at most RS rows of one item; a stage's barrier `full` completes once all
+// of its bytes have landed.  The kWarps consumer warps scan the staged rows
+// (one 16-byte column group per thread, R row groups; a row's own cost
+// CM(d, c) is read from the staged row itself) and release the stage on its
+// barrier `empty`.  At the end of an item, or of the part of it in this
+// CTA's range, the consumers fold their partial minima (barrier `fold`,
+// double-buffered) while the producer goes on filling stages.  Every wait is
+// bounded: past kScanWaitLimitNs the waiter sets ctl[BT_ERR] and leaves (the
+// producer first waits, bounded, for its copies in flight), and bt_unpack
+// then marks the whole table.
+constexpr int kBulkMinRowBytes = 512;
+constexpr int kStageBytes = 32768;       // target bytes per stage (the producer's cost is per stage)
+constexpr int kSmemLimit = 232448;       // dynamic shared memory of one CTA (227 KB)
+constexpr int kMaxStages = 16;
+constexpr int kIdsWin = 1024;            // unit ids per window (two windows in shared memory)
+constexpr int kRedBytes = kThreads * 32; // one fold buffer: R*S*VPL keys (int16) or pairs (int32)
+constexpr int kBulkThreads = kThreads + 32;
+constexpr int kFoldCols = 8;             // columns per consumer thread in a fold (k <= 4096)
+constexpr uint64_t kScanWaitLimitNs = 1000000000ull;
+constexpr uint32_t kScanSleepNs = 1000000;
 
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(sdst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gsrc) : "memory");
+struct StageMeta {
+  int32_t c;      // center of the rows
+  int32_t r0;     // position in perm of the first row of the fold unit
+  int32_t j;      // position of the stage's first row inside the fold unit
+  int32_t rows;   // rows in the stage; -1 marks the end of the work
+  int32_t last;   // the stage ends its fold unit
+  int32_t pad0, pad1, pad2;
+};
+
+struct BulkShape {
+  int S, R, RS, NS, row_bytes, stage_bytes;
+};
+
+__host__ __device__ inline size_t seg_smem_bytes(int32_t k) { return ((4 * (size_t)(k + 1)) + 15) & ~(size_t)15; }
+
+// Shared memory besides the stages (fold buffers, id windows, segment
+// starts, stage descriptors and barriers, the latter two at their largest).
+static size_t bulk_fixed_bytes(int32_t k) {
+  return 2 * (size_t)kRedBytes + 8 * (size_t)kIdsWin + seg_smem_bytes(k) +
+         (size_t)kMaxStages * sizeof(StageMeta) + (2 * (size_t)kMaxStages + 3) * 8;
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-size_t bt_staged_smem_bytes() {
-  return (size_t)kStages * kThreads * 16 + (size_t)kThreads * 8 * sizeof(int2);
+static BulkShape bulk_shape(int32_t k, int elem) {
+  BulkShape p;
+  const int VPL = 16 / elem;
+  p.S = (k + VPL - 1) / VPL;
+  p.R = kThreads / p.S;
+  p.row_bytes = p.S * 16;
+  const int per = std::max(1, kStageBytes / p.row_bytes);
+  p.RS = std::min(32, std::max(p.R, per / p.R * p.R));
+  p.stage_bytes = p.RS * p.row_bytes;
+  p.NS = std::max(2, std::min<int>(kMaxStages, (int)((kSmemLimit - bulk_fixed_bytes(k)) / p.stage_bytes)));
+  return p;
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
-bt_scan_rows_staged16(const int16_t* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
-                      const int32_t* __restrict__ perm, const int32_t* __restrict__ ownv,
-                      const int32_t* __restrict__ item_off, const int4* __restrict__ items,
-                      unsigned long long* t64, int* work) {
-  constexpr int VPL = 8, P = kStages;
-  extern __shared__ __align__(16) unsigned char dsm[];
-  uint4* stage = reinterpret_cast<uint4*>(dsm);                           // [P][kThreads]
-  int2* red = reinterpret_cast<int2*>(dsm + (size_t)P * kThreads * 16);  // [kThreads * VPL]
-  __shared__ int s_item[2];
-  const int S = (k + VPL - 1) / VPL;
-  const int R = kThreads / S;
-  const int tid = threadIdx.x, slot = tid % S, g = tid / S;
-  const int32_t total = item_off[k];
-  if (tid == 0) s_item[0] = atomicAdd(work, 1);
+static size_t bulk_smem_bytes(const BulkShape& p, int32_t k) {
+  return (size_t)p.NS * p.stage_bytes + 2 * (size_t)kRedBytes + 8 * (size_t)kIdsWin +
+         seg_smem_bytes(k) + (size_t)p.NS * sizeof(StageMeta) + (2 * (size_t)p.NS + 3) * 8;
+}
+
+// Largest dynamic shared memory any shape needs (the attribute set once).
+static size_t bulk_smem_max() { return kSmemLimit; }
+
+__device__ __forceinline__ bool scan_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = gtimer_ns();
+  while (!mbar_try_wait(bar, parity, kScanSleepNs))
+    if (gtimer_ns() - t0 > kScanWaitLimitNs) return false;
+  return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBulkThreads, 1)
+bt_scan_bulk(const T* __restrict__ cm, int64_t ld, int32_t k, const int32_t* __restrict__ perm,
+             const int32_t* __restrict__ seg, unsigned long long* t64, int* ctl, BulkShape p) {
+  constexpr int VPL = 16 / (int)sizeof(T);
+  extern __shared__ __align__(128) unsigned char dsm[];
+  const int NS = p.NS, SB = p.stage_bytes, RB = p.row_bytes;
+  unsigned char* stages = dsm;
+  unsigned char* redb = dsm + (size_t)NS * SB;
+  int32_t* s_ids = reinterpret_cast<int32_t*>(redb + 2 * kRedBytes);       // 2 windows
+  int32_t* s_seg = s_ids + 2 * kIdsWin;                                    // k + 1
+  StageMeta* meta = reinterpret_cast<StageMeta*>(reinterpret_cast<unsigned char*>(s_seg) +
+                                                 seg_smem_bytes(k));
+  uint64_t* full = reinterpret_cast<uint64_t*>(meta + NS);
+  uint64_t* empty = full + NS;
+  uint64_t* fold = empty + NS;
+  uint64_t* idsbar = fold + 1;                                             // 2
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int32_t rows_total = ctl[BT_ROWS], chunk = ctl[BT_CHUNK];
+  const int32_t P0 = (int32_t)((int64_t)blockIdx.x * rows_total / gridDim.x);
+  const int32_t P1 = (int32_t)((int64_t)(blockIdx.x + 1) * rows_total / gridDim.x);
+  if (tid < NS) {
+    mbar_init(&full[tid], 1);
+    mbar_init(&empty[tid], kWarps);
+  }
+  if (tid == 0) {
+    mbar_init(fold, kWarps);
+    mbar_init(&idsbar[0], 1);
+    mbar_init(&idsbar[1], 1);
+    mbar_fence_init();
+  }
+  for (int i = tid; i <= k; i += kBulkThreads) s_seg[i] = seg[i];
   __syncthreads();
-  for (int32_t item = s_item[0];;) {
-    if (item >= total) break;
-    const int4 desc = items[item];
-    if (tid == 0) s_item[1] = atomicAdd(work, 1);
-    const int32_t c = desc.x, r0 = desc.y, cnt = desc.z;
-    uint32_t key[VPL];
-#pragma unroll
-    for (int q = 0; q < VPL; ++q) key[q] = 0xffffffffu;
-    if (g < R && g < cnt) {
-      const int32_t M = (cnt - g + R - 1) / R;        // rows of this thread: g + m * R
-      auto row_id = [&](int32_t m) -> int32_t {
-        return m < M ? (int32_t)min((uint32_t)__ldg(perm + r0 + g + m * R), (uint32_t)(n - 1)) : 0;
-      };
-      auto row_own = [&](int32_t m) -> int32_t { return m < M ? __ldg(ownv + r0 + g + m * R) : 0; };
-      int32_t idA[P], ownA[P], idB[P], ownB[P], ownS[P];
-      // rows 0..P-1 go to the stages now, rows P..2P-1 and 2P..3P-1 are prefetched
-#pragma unroll
-      for (int q = 0; q < P; ++q) {
-        const int32_t d0 = row_id(q);
-        ownS[q] = row_own(q);
-        if (q < M) cp_async16(&stage[q * kThreads + tid], cm + (int64_t)d0 * ld + slot * VPL);
-        cp_async_commit();
-        idA[q] = row_id(P + q);
-        ownA[q] = row_own(P + q);
-        idB[q] = row_id(2 * P + q);
-        ownB[q] = row_own(2 * P + q);
+
+  if (warp == kWarps) {
+    // ---------------------------------------------------------- producer
+    const int32_t A = P0 & ~3;                        // 16-byte aligned start of the id windows
+    const int nwin = P1 > P0 ? (P1 - A + kIdsWin - 1) / kIdsWin : 0;
+    int issued = -1, ready = -1;                      // id windows copied / waited for
+    int s = 0, fills = 0;
+    uint32_t eph = 0;                                 // slot s is free once phase eph ^ 1 completed
+    bool ok = true;
+    // center of P0: the largest c with seg[c] <= P0 (it is not empty)
+    int c = 0;
+    if (P0 < P1) {
+      int lo = 0, hi = k - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_seg[mid] <= P0) lo = mid; else hi = mid - 1;
       }
-      for (int32_t m = 0; m < M; m += P) {
-#pragma unroll
-        for (int q = 0; q < P; ++q) {
-          cp_async_wait<P - 1>();                     // row m + q has landed
-          if (m + q < M) {
-            const uint4 wv = stage[q * kThreads + tid];
-            const uint32_t crow = ((uint32_t)(32768 - ownS[q]) << 16) | (uint32_t)(g + (m + q) * R);
-            const uint32_t w4[4] = {wv.x, wv.y, wv.z, wv.w};
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              key[2 * h] = min(key[2 * h], (w4[h] << 16) + crow);
-              key[2 * h + 1] = min(key[2 * h + 1], (w4[h] & 0xffff0000u) + crow);
+      c = lo;
+    }
+    int32_t sb = s_seg[c], se = s_seg[c + 1];
+    int32_t win_end = A;                              // ids below this position have landed
+    int32_t pos = P0;
+    // one fold unit per pass: the part of an item inside [P0, P1)
+    while (ok && pos < P1) {
+      while (se <= pos) { ++c; sb = s_seg[c]; se = s_seg[c + 1]; }
+      const int32_t u0 = pos;
+      const int32_t len = min(min(se, sb + ((pos - sb) / chunk + 1) * chunk), P1) - u0;
+      for (int32_t j = 0; j < len; j += p.RS) {
+        const int rows = min(p.RS, len - j);
+        const int32_t q = u0 + j;
+        if (q + rows > win_end || (issued < nwin - 1 && q >= A + issued * kIdsWin)) {
+          // the window after q's goes out as soon as q enters q's window (its
+          // buffer held the window before q's, whose rows are all issued);
+          // then wait for the windows this stage reads
+          const int wlast = min((q - A) / kIdsWin + 1, nwin - 1);
+          while (issued < wlast) {
+            ++issued;
+            if (lane == 0) {
+              const int32_t first = A + issued * kIdsWin;
+              const uint32_t bytes = ((uint32_t)min(kIdsWin, P1 - first) * 4u + 15u) & ~15u;
+              fence_proxy_async_smem();
+              mbar_arrive_expect(&idsbar[issued & 1], bytes);
+              bulk_load_smem(smem_u32(s_ids + (issued & 1) * kIdsWin), perm + first, bytes,
+                             smem_u32(&idsbar[issued & 1]));
             }
           }
-          // stage q now takes row m + q + P
-          if (m + q + P < M) cp_async16(&stage[q * kThreads + tid], cm + (int64_t)idA[q] * ld + slot * VPL);
-          cp_async_commit();
-          ownS[q] = ownA[q];
-          idA[q] = idB[q];
-          ownA[q] = ownB[q];
-          idB[q] = row_id(m + q + 3 * P);
-          ownB[q] = row_own(m + q + 3 * P);
+          const int wneed = (q + rows - 1 - A) / kIdsWin;
+          while (ok && ready < wneed) {
+            ++ready;
+            ok = scan_wait(&idsbar[ready & 1], (ready >> 1) & 1);
+          }
+          win_end = A + (ready + 1) * kIdsWin;
+          if (!ok) break;
+        }
+        if (!scan_wait(&empty[s], eph ^ 1)) { ok = false; break; }
+        if (lane == 0) {
+          StageMeta m;
+          m.c = c; m.r0 = u0; m.j = j; m.rows = rows; m.last = j + p.RS >= len;
+          m.pad0 = m.pad1 = m.pad2 = 0;
+          meta[s] = m;
+          mbar_arrive_expect(&full[s], (uint32_t)(rows * RB));
+        }
+        __syncwarp();
+        const uint32_t dst = smem_u32(stages + (size_t)s * SB);
+        for (int i = lane; i < rows; i += 32) {
+          const int32_t d = s_ids[(q + i - A) & (2 * kIdsWin - 1)];
+          bulk_load_smem(dst + (uint32_t)(i * RB), cm + (int64_t)d * ld, (uint32_t)RB,
+                         smem_u32(&full[s]));
+        }
+        ++fills;
+        if (++s == NS) { s = 0; eph ^= 1; }
+      }
+      pos = u0 + len;
+    }
+    if (ok) {
+      if (scan_wait(&empty[s], eph ^ 1)) {
+        if (lane == 0) {
+          meta[s].rows = -1;     // end of the work
+          mbar_arrive(&full[s]);
+        }
+      } else {
+        ok = false;
+      }
+    }
+    if (!ok) {
+      if (lane == 0) atomicExch(&ctl[BT_ERR], 1);
+      // copies still in flight: the last NS stage fills and unwaited id windows
+      for (int f = max(0, fills - NS); f < fills; ++f) scan_wait(&full[f % NS], (f / NS) & 1);
+      for (int w = ready + 1; w <= issued; ++w) scan_wait(&idsbar[w & 1], (w >> 1) & 1);
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------ consumers
+  const int S = p.S, R = p.R;
+  const int slot = tid % S, g = tid / S;
+  const bool act = g < R;
+  int s = 0, rb = 0;
+  uint32_t fph = 0, cph = 0;
+  uint32_t key[VPL];
+  int32_t bt[VPL], br[VPL];
+#pragma unroll
+  for (int q = 0; q < VPL; ++q) { key[q] = 0xffffffffu; bt[q] = kTInf; br[q] = -1; }
+  for (;;) {
+    if (!scan_wait(&full[s], fph)) {
+      if (lane == 0) atomicExch(&ctl[BT_ERR], 1);
+      break;
+    }
+    const StageMeta m = meta[s];
+    if (m.rows < 0) break;
+    if (act) {
+      const unsigned char* sbase = stages + (size_t)s * SB;
+      for (int i = g; i < m.rows; i += R) {
+        const T* row = reinterpret_cast<const T*>(sbase + (size_t)i * RB);
+        const int32_t own = (int32_t)row[m.c];
+        const uint4 wv = reinterpret_cast<const uint4*>(row)[slot];
+        const int32_t ri = m.j + i;
+        if constexpr (sizeof(T) == 2) {
+          const uint32_t crow = ((uint32_t)(32768 - own) << 16) | (uint32_t)ri;
+          const uint32_t w4[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            key[2 * h] = min(key[2 * h], (w4[h] << 16) + crow);
+            key[2 * h + 1] = min(key[2 * h + 1], (w4[h] & 0xffff0000u) + crow);
+          }
+        } else {
+          const int32_t w4[4] = {(int32_t)wv.x, (int32_t)wv.y, (int32_t)wv.z, (int32_t)wv.w};
+#pragma unroll
+          for (int q = 0; q < VPL; ++q) {
+            const int32_t t = w4[q] - own;
+            if (t < bt[q]) { bt[q] = t; br[q] = ri; }
+          }
         }
       }
-      cp_async_wait<0>();
     }
-    if (g < R) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+    if (++s == NS) { s = 0; fph ^= 1; }
+    if (!m.last) continue;
+    // end of a fold unit: fold the row groups, merge into the table
+    unsigned char* red = redb + (size_t)rb * kRedBytes;
+    if (act) {
 #pragma unroll
       for (int q = 0; q < VPL; ++q) {
-        int32_t bt = kTInf, bd = -1;
-        if (key[q] != 0xffffffffu) {
-          bt = (int32_t)(key[q] >> 16) - 32768;
-          bd = (int32_t)min((uint32_t)__ldg(perm + r0 + (int32_t)(key[q] & 0xffffu)), (uint32_t)(n - 1));
+        const int at = g * S * VPL + slot * VPL + q;
+        if constexpr (sizeof(T) == 2) reinterpret_cast<uint32_t*>(red)[at] = key[q];
+        else reinterpret_cast<int2*>(red)[at] = make_int2(bt[q], br[q]);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(fold);
+    if (!scan_wait(fold, cph)) {
+      if (lane == 0) atomicExch(&ctl[BT_ERR], 1);
+      break;
+    }
+    cph ^= 1;
+    int32_t ft[kFoldCols], fr[kFoldCols];
+#pragma unroll
+    for (int q = 0; q < kFoldCols; ++q) {
+      const int col = tid + q * kThreads;
+      ft[q] = kTInf;
+      fr[q] = -1;
+      if (col < k) {
+        if constexpr (sizeof(T) == 2) {
+          uint32_t b = 0xffffffffu;
+          for (int gg = 0; gg < R; ++gg)
+            b = min(b, reinterpret_cast<const uint32_t*>(red)[gg * S * VPL + col]);
+          if (b != 0xffffffffu) { ft[q] = (int32_t)(b >> 16) - 32768; fr[q] = (int32_t)(b & 0xffffu); }
+        } else {
+          for (int gg = 0; gg < R; ++gg) {
+            const int2 e = reinterpret_cast<const int2*>(red)[gg * S * VPL + col];
+            if (e.y >= 0 && (fr[q] < 0 || e.x < ft[q] || (e.x == ft[q] && e.y < fr[q]))) {
+              ft[q] = e.x;
+              fr[q] = e.y;
+            }
+          }
         }
-        red[g * S * VPL + slot * VPL + q] = make_int2(bt, bd);
       }
     }
-    __syncthreads();
-    for (int col = tid; col < k; col += kThreads) {
-      int32_t t = kTInf, dd = -1;
-      for (int gg = 0; gg < R; ++gg) {
-        const int2 e = red[gg * S * VPL + col];
-        if (lex_less(e.x, e.y, t, dd)) { t = e.x; dd = e.y; }
-      }
-      if (dd >= 0 && col != c) {
-        const unsigned long long kk =
-            ((unsigned long long)(uint32_t)(t + (int64_t)2147483648LL) << 32) | (uint32_t)dd;
-        atomicMin(&t64[(int64_t)c * k + col], kk);
+    int32_t fd[kFoldCols];
+#pragma unroll
+    for (int q = 0; q < kFoldCols; ++q) fd[q] = fr[q] >= 0 ? perm[m.r0 + fr[q]] : -1;
+#pragma unroll
+    for (int q = 0; q < kFoldCols; ++q) {
+      const int col = tid + q * kThreads;
+      if (fr[q] >= 0 && col != m.c) {
+        const unsigned long long pk =
+            ((unsigned long long)(uint32_t)(ft[q] + (int64_t)2147483648LL) << 32) | (uint32_t)fd[q];
+        atomicMin(&t64[(int64_t)m.c * k + col], pk);
       }
     }
-    item = s_item[1];
-    __syncthreads();
-    if (tid == 0) s_item[0] = item;
+    rb ^= 1;
+#pragma unroll
+    for (int q = 0; q < VPL; ++q) { key[q] = 0xffffffffu; bt[q] = kTInf; br[q] = -1; }
   }
 }
 
 __global__ void __launch_bounds__(kThreads) bt_unpack(const unsigned long long* __restrict__ t64,
                                                       int32_t k, int32_t* tc, int32_t* td,
-                                                      const int* err) {
-  const bool bad = *err != 0;   // reserved error flag: marks the whole table
+                                                      const int* ctl) {
+  const bool bad = ctl[BT_ERR] != 0;   // a scan wait ran out: the whole table is marked
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < (int64_t)k * k;
        i += (int64_t)gridDim.x * kThreads) {
     const unsigned long long e = t64[i];
@@ -548,59 +710,56 @@ __global__ void __launch_bounds__(kThreads) bt_unpack(const unsigned long long* 
 
 int bt_max_k(int elem_bytes) { return kThreads * (16 / elem_bytes); }
 
+// Sets the bulk scan's dynamic shared memory limit once per device.
+template <typename T>
+static cudaError_t bulk_attr() {
+  static std::atomic<uint64_t> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!(done.load() & (1ull << dev))) {
+    e = cudaFuncSetAttribute(bt_scan_bulk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bulk_smem_max());
+    if (e != cudaSuccess) return e;
+    done.fetch_or(1ull << dev);
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t scan_launch(const T* cm, int64_t ld, int32_t n, int32_t k, const BtWorkspace& W,
+                               cudaStream_t st, int num_sms) {
+  const BulkShape p = bulk_shape(k, (int)sizeof(T));
+  if (p.row_bytes >= kBulkMinRowBytes) {
+    const cudaError_t e = bulk_attr<T>();
+    if (e != cudaSuccess) return e;
+    bt_scan_bulk<T><<<num_sms, kBulkThreads, bulk_smem_bytes(p, k), st>>>(cm, ld, k, W.perm, W.cnt,
+                                                                           W.t64, W.ctl, p);
+  } else {
+    bt_scan_rows<T><<<num_sms, kThreads, 0, st>>>(cm, ld, n, k, W.perm, W.items, W.t64, W.ctl);
+  }
+  return cudaSuccess;
+}
+
 // Returns a cudaError_t (cudaSuccess on success); argument checks are done
 // by the caller.
 cudaError_t best_transfer_run(int32_t n, int32_t k, const void* cm, int elem_bytes, int64_t ld,
                               const int32_t* assign, int32_t* tc, int32_t* td, void* ws,
                               cudaStream_t st, int num_sms) {
   void* base = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
-  BtWorkspace W = carve(base, n, k);
-  const int grid_lin = num_sms * 4;
-  bt_init_keys<<<grid_lin, kThreads, 0, st>>>(assign, n, k, W.k0, W.v0);
-  const int bits = 32 - __builtin_clz((unsigned)k);   // keys in [0, k]
-  const int passes = (bits + 7) / 8;
-  int32_t *sk = W.k0, *sv = W.v0, *dk = W.k1, *dv = W.v1;
-  for (int p = 0; p < passes; ++p) {
-    bt_hist<<<(unsigned)W.ntiles, kThreads, 0, st>>>(sk, n, 8 * p, W.tile_hist, W.ntiles);
-    bt_digit_sums<<<256, kThreads, 0, st>>>(W.tile_hist, W.ntiles, W.dsum);
-    bt_digit_scan<<<256, kThreads, 0, st>>>(W.tile_hist, W.ntiles, W.dsum);
-    bt_scatter<<<(unsigned)W.ntiles, kThreads, 0, st>>>(sk, sv, dk, dv, n, 8 * p, W.tile_hist,
-                                                        W.ntiles);
-    std::swap(sk, dk);
-    std::swap(sv, dv);
-  }
-  cudaMemsetAsync(W.seg_start, 0, 4ull * k, st);
-  cudaMemsetAsync(W.seg_end, 0, 4ull * k, st);
-  bt_bounds<<<grid_lin, kThreads, 0, st>>>(sk, sv, n, k, W.seg_start, W.seg_end,
-                                            elem_bytes == 2 ? static_cast<const int16_t*>(cm)
-                                                            : nullptr,
-                                            ld, W.ownv);
-  bt_items<<<grid_lin, kThreads, 0, st>>>(W.seg_start, W.seg_end, k, W.item_off, W.t64);
-  bt_scan<<<1, kThreads, 0, st>>>(W.item_off, k, W.item_off + k);
-  const int grid_scan = num_sms;
-  cudaMemsetAsync(W.err, 0, 2 * sizeof(int), st);
-  bt_item_list<<<grid_lin, kThreads, 0, st>>>(W.seg_start, W.seg_end, W.item_off, k, W.items);
-  if (elem_bytes == 2) {
-    // the staged kernel's dynamic shared memory, set once per device
-    static std::atomic<uint64_t> attr_set{0};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!(attr_set.load() & (1ull << dev))) {
-      e = cudaFuncSetAttribute(bt_scan_rows_staged16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)bt_staged_smem_bytes());
-      if (e != cudaSuccess) return e;
-      attr_set.fetch_or(1ull << dev);
-    }
-    bt_scan_rows_staged16<<<grid_scan, kThreads, bt_staged_smem_bytes(), st>>>(
-        static_cast<const int16_t*>(cm), ld, n, k, sv, W.ownv, W.item_off, W.items, W.t64,
-        W.err + 1);
-  } else {
-    bt_scan_rows<int32_t><<<grid_scan, kThreads, 0, st>>>(
-        static_cast<const int32_t*>(cm), ld, n, k, sv, W.item_off, W.items, W.t64, W.err + 1);
-  }
-  bt_unpack<<<grid_lin, kThreads, 0, st>>>(W.t64, k, tc, td, W.err);
+  const BtWorkspace W = carve(base, n, k);
+  cudaError_t e = cudaMemsetAsync(W.ctl, 0, 4 * BT_CTL_WORDS + 4ull * (k + 1), st);
+  if (e != cudaSuccess) return e;
+  bt_count<<<kTiles, kTileThreads, 4 * (size_t)k, st>>>(assign, n, k, W.cnt, W.tile_rel);
+  bt_plan<<<1, kThreads, 0, st>>>(W.cnt, k, num_sms, W.items, W.ctl);
+  bt_place<<<kTiles, kTileThreads, 4 * (size_t)k, st>>>(assign, n, k, W.cnt, W.tile_rel, W.perm);
+  bt_sort_items<<<num_sms * 4, kThreads, 0, st>>>(W.items, W.ctl, W.perm, k, W.t64);
+  e = elem_bytes == 2
+          ? scan_launch(static_cast<const int16_t*>(cm), ld, n, k, W, st, num_sms)
+          : scan_launch(static_cast<const int32_t*>(cm), ld, n, k, W, st, num_sms);
+  if (e != cudaSuccess) return e;
+  bt_unpack<<<num_sms * 4, kThreads, 0, st>>>(W.t64, k, tc, td, W.ctl);
   return cudaGetLastError();
 }
 

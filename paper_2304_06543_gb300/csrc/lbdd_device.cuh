@@ -221,6 +221,21 @@ __device__ __forceinline__ void bulk_copy_to_cta(uint32_t dst, const void* src, 
       "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
       ::"r"(dst), "r"(smem_u32(src)), "r"(bytes), "r"(bar) : "memory");
 }
+// One arrival on a barrier of this CTA (release: this thread's earlier
+// shared-memory reads and writes are ordered before the phase completes).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// from global memory into this CTA's shared memory (address `dst`),
+// completing the bytes on this CTA's barrier at shared address `bar`.
+__device__ __forceinline__ void bulk_load_smem(uint32_t dst, const void* src, uint32_t bytes,
+                                               uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
 // 16 bytes into another CTA's shared memory (cluster address `dst`),
 // completing that many bytes on its barrier at cluster address `bar`.
 __device__ __forceinline__ void st_async16(uint32_t dst, int4 v, uint32_t bar) {

@@ -148,3 +148,69 @@ def test_large_snapshot_full_size(gpu_lib):
     _check_witnesses(inst, smin, tc, td)
     rng = np.random.default_rng(3)
     _check_sampled_rows(inst, smin, tc, td, rng.choice(k, 16, replace=False))
+
+
+# Row widths on both sides of the 512-byte switch between the register scan
+# and the bulk-copy scan, the largest k of each storage type, and allotments
+# with many equal costs (scale 3: CM in 1..6) where one center holds most
+# units, so that its rows are split over many work items and equal-cost
+# candidates from different items meet in the table merge.
+SHAPE_CASES = [  # (n, k, dtype, scale, skew)
+    (9000, 256, "i16", 100.0, False),     # 512-byte rows: bulk copies
+    (9000, 248, "i16", 100.0, False),     # 496-byte rows: register scan
+    (9000, 128, "i32", 100.0, False),
+    (9000, 124, "i32", 100.0, False),
+    (6000, 4096, "i16", 1000.0, False),   # largest int16 k: one row group
+    (6000, 2048, "i32", 1000.0, False),   # largest int32 k
+    (40000, 300, "i16", 3.0, True),
+    (40000, 300, "i32", 3.0, True),
+    (40000, 40, "i16", 3.0, True),
+    (2, 600, "i16", 3.0, False),
+]
+
+
+@pytest.mark.parametrize("case", range(len(SHAPE_CASES)))
+def test_scan_shapes_and_ties(gpu_lib, case):
+    n, k, dtype, scale, skew = SHAPE_CASES[case]
+    inst = L.make_named("city", dtype=dtype, n=n, k=k, seed=8100 + case, scale=scale,
+                        cap_frac=max(0.8, 2.0 * k / n))   # capacities need a total >= k
+    assert inst.cm.min() >= 1
+    assign = inst.cm.argmin(axis=1).astype(np.int32)
+    if skew:
+        rng = np.random.default_rng(case)
+        assign[rng.random(n) < 0.6] = 3 % k        # one center takes ~60% of the units
+        assign[rng.random(n) < 0.05] = -1
+    tc, td = gpu_table(gpu_lib, inst, assign, dtype)
+    rtc, rtd = ref_table(inst, assign)
+    assert np.array_equal(tc, rtc)
+    assert np.array_equal(td, rtd)
+    assert (td != -2).all()                        # no scan wait ran out
+
+
+def test_scan_repeated_calls_share_a_workspace(gpu_lib):
+    """Two different allotments through one workspace, int16 then int32: each
+    call rewrites every scratch word it reads."""
+    import torch
+    lb = gpu_lib
+    inst = L.make_named("city", dtype="i16", n=20000, k=500, seed=8200, scale=50.0)
+    n, k = inst.n, inst.k
+    wsb = lb.best_transfer_workspace(n, k)
+    ws = torch.full((wsb,), 0x5A, dtype=torch.uint8, device="cuda")
+    a1 = inst.cm.argmin(axis=1).astype(np.int32)
+    a2 = np.random.default_rng(1).integers(-1, k, n).astype(np.int32)
+    for dtype, assign in (("i16", a1), ("i32", a2), ("i16", a2), ("i32", a1)):
+        cmd = lb.CM_I16 if dtype == "i16" else lb.CM_I32
+        tdt = torch.int16 if dtype == "i16" else torch.int32
+        ld = lb.cm_pitch(k, cmd)
+        host = np.zeros((n, ld), inst.cm.dtype if dtype == "i16" else np.int32)
+        host[:, :k] = inst.cm
+        buf = torch.zeros(n * ld + 128, dtype=tdt, device="cuda")
+        buf[: n * ld].copy_(torch.from_numpy(host.reshape(-1)).to(tdt))
+        a = torch.from_numpy(assign).cuda()
+        tc = torch.empty(k * k, dtype=torch.int32, device="cuda")
+        td = torch.empty(k * k, dtype=torch.int32, device="cuda")
+        lb.best_transfer(n, k, buf, cmd, ld, a, tc, td, ws, wsb)
+        torch.cuda.synchronize()
+        rtc, rtd = ref_table(inst, assign)
+        assert np.array_equal(tc.cpu().numpy().reshape(k, k), rtc)
+        assert np.array_equal(td.cpu().numpy().reshape(k, k), rtd)
