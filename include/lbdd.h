@@ -387,7 +387,7 @@ int lbdd_best_transfer(int32_t n, int32_t k, const void* cm_dev, int cm_dtype, i
  *   caller's device buffers), without the workspace.
  *   Limit: lbdd_best_transfer_workspace(n, k) must not exceed 64 MiB, else
  *   LBDD_ERR_BUDGET is returned and nothing is launched (the city-scale
- *   200,000 x 500 case needs 2,988,800 bytes, about 2.9 MiB).
+ *   200,000 x 500 case needs 34,988,800 bytes, about 33.4 MiB).
  *   The first call on each device looks up the device address of the array
  *   (with that device current); make that first call before any stream
  *   capture.

@@ -29,6 +29,12 @@
 //   6. bt_unpack: the (tc, td) int32 pair.
 // Step 5 reads every CM byte of the allotted rows once and is the HBM-bound
 // kernel; the other steps move O(n + k*k) bytes.
+//
+// int16 costs with 256 to 512 centers take a shorter path with no grouping
+// (rows of 512 bytes to 1 KB gather poorly): bt_own, then bt_scan_stream16
+// reads the CM in row order, one 64-column slice and one row range per CTA,
+// keeping the minima in shared memory, and bt_merge_ranges combines the
+// ranges into (tc, td).
 #include <atomic>
 #include <algorithm>
 
@@ -54,8 +60,22 @@ struct BtWorkspace {
   int32_t* perm;                // n (+ 4 readable): allotted units grouped by center
   int4* items;                  // n / kChunkMin + k + 1 items {center, first row, rows, 0}
   unsigned long long* t64;      // k x k packed ((cost + 2^31) << 32) | d
+  uint32_t* part;               // row-order int16 path: one k x k key table per row range
   size_t bytes;
 };
+
+// Row-order int16 path (bt_scan_stream16): centers in [kStreamMinK,
+// kStreamMaxK], at most kStreamMaxRanges row ranges of at most
+// kStreamRowSpan rows each.
+constexpr int kStreamMinK = 256, kStreamMaxK = 512;
+constexpr int kStreamCols = 64;          // columns per slice: 128 bytes of a row
+constexpr int kStreamMaxRanges = 32;
+constexpr int64_t kStreamRowSpan = 65536;  // the 16-bit row offset of a key
+
+static size_t stream_part_bytes(int32_t n, int32_t k) {
+  if (k < kStreamMinK || k > kStreamMaxK) return 0;
+  return 4ull * k * k * (size_t)std::min<int32_t>(kStreamMaxRanges, n);
+}
 
 static inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -74,6 +94,7 @@ static BtWorkspace carve(void* base, int32_t n, int32_t k) {
   W.perm = reinterpret_cast<int32_t*>(take(4ull * n + 16));   // id windows round up to 16 bytes
   W.items = reinterpret_cast<int4*>(take(16ull * ((size_t)n / kChunkMin + (size_t)k + 1)));
   W.t64 = reinterpret_cast<unsigned long long*>(take(8ull * k * k));
+  W.part = reinterpret_cast<uint32_t*>(take(stream_part_bytes(n, k)));
   W.bytes = o;
   return W;
 }
@@ -708,6 +729,141 @@ __global__ void __launch_bounds__(kThreads) bt_unpack(const unsigned long long* 
   }
 }
 
+// ----------------------------------------------------- row-order int16 ---
+//
+// int16 rows of kStreamMinK..kStreamMaxK centers (512 bytes to 1 KB) are
+// short for row gathers, so this path reads the CM in row order instead and
+// needs no grouping.  CTA (j, r) owns the 64-column slice j and the row range
+// r, and keeps in shared memory one 32-bit key per (center, column of the
+// slice): ((t + 32768) << 16) | (d - first row of the range), so the smaller
+// key is the lexicographically smaller (t, d) inside the range.  A thread
+// reads 16 bytes (8 columns) of kStreamUnroll rows at once, compares its keys
+// with the table and lowers an entry with a shared atomicMin only where its
+// key is smaller (entries only decrease, so a stale read never hides a
+// smaller key).  A table row is laid out as two halves: the first 4 columns
+// of every thread's 8 at words 4 * cg, the other 4 at 32 + 4 * cg, so each
+// 128-bit shared load of 8 threads covers 32 distinct banks.  bt_own gathers
+// CM(d, assign[d]) first; bt_merge_ranges takes, for every (u, v), the
+// smallest t over the ranges in range order (ranges ascend in d, so the first
+// range that attains it holds the smallest d) and writes tc/td.
+constexpr int kStreamUnroll = 6;
+
+// Row ranges of the row-order path on `num_sms` SMs, 0 if it does not apply.
+static int stream_ranges(int32_t n, int32_t k, int num_sms) {
+  if (k < kStreamMinK || k > kStreamMaxK) return 0;
+  const int64_t need = ((int64_t)n + kStreamRowSpan - 1) / kStreamRowSpan;
+  if (need > kStreamMaxRanges) return 0;
+  const int nslice = (k + kStreamCols - 1) / kStreamCols;
+  int64_t r = std::max<int64_t>(need, num_sms / nslice);
+  r = std::min<int64_t>(r, kStreamMaxRanges);
+  r = std::min<int64_t>(r, n);
+  return (int)r;
+}
+
+__global__ void __launch_bounds__(kThreads) bt_own(const int32_t* __restrict__ assign, int32_t n,
+                                                   int32_t k, const int16_t* __restrict__ cm,
+                                                   int64_t ld, int32_t* own) {
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads) {
+    const int32_t a = assign[i];
+    own[i] = (a >= 0 && a < k) ? (int32_t)cm[i * ld + a] : 0;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+bt_scan_stream16(const int16_t* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
+                 const int32_t* __restrict__ assign, const int32_t* __restrict__ own, int nslice,
+                 int nranges, uint32_t* part) {
+  constexpr int U = kStreamUnroll;
+  extern __shared__ __align__(16) uint32_t acc[];   // k rows of kStreamCols keys
+  const int tid = threadIdx.x, cg = tid & 7, rl = tid >> 3;
+  const int j = blockIdx.x % nslice, r = blockIdx.x / nslice;
+  const int64_t R0 = (int64_t)r * n / nranges, R1 = (int64_t)(r + 1) * n / nranges;
+  const int c0 = j * kStreamCols;
+  const int w = min(kStreamCols, k - c0);
+  const bool act = cg * 8 < w;
+  const uint4 none = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+  for (int i = tid; i < k * kStreamCols / 4; i += kThreads) reinterpret_cast<uint4*>(acc)[i] = none;
+  __syncthreads();
+  const int16_t* colp = cm + c0 + cg * 8;
+  // two register batches of U rows: the next batch's loads are in flight
+  // while the current one is compared
+  auto load = [&](int64_t b, uint4* x, int32_t* a, int32_t* o) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t d = b + 64 * u;
+      const bool v = d < R1;
+      a[u] = v ? __ldg(assign + d) : -1;
+      o[u] = v ? __ldg(own + d) : 0;
+      x[u] = (v && act) ? __ldg(reinterpret_cast<const uint4*>(colp + d * ld)) : make_uint4(0, 0, 0, 0);
+    }
+  };
+  auto fold = [&](int64_t b, const uint4* x, const int32_t* a, const int32_t* o) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!act || a[u] < 0 || a[u] >= k) continue;
+      const uint32_t crow = ((uint32_t)(32768 - o[u]) << 16) | (uint32_t)(b + 64 * u - R0);
+      uint32_t* row = acc + a[u] * kStreamCols;
+      uint32_t* lo_p = row + 4 * cg;
+      uint32_t* hi_p = row + 32 + 4 * cg;
+      const uint4 lo = *reinterpret_cast<const uint4*>(lo_p);
+      const uint4 hi = *reinterpret_cast<const uint4*>(hi_p);
+      const uint32_t k0 = (x[u].x << 16) + crow, k1 = (x[u].x & 0xffff0000u) + crow;
+      const uint32_t k2 = (x[u].y << 16) + crow, k3 = (x[u].y & 0xffff0000u) + crow;
+      const uint32_t k4 = (x[u].z << 16) + crow, k5 = (x[u].z & 0xffff0000u) + crow;
+      const uint32_t k6 = (x[u].w << 16) + crow, k7 = (x[u].w & 0xffff0000u) + crow;
+      if (k0 < lo.x) atomicMin(lo_p + 0, k0);
+      if (k1 < lo.y) atomicMin(lo_p + 1, k1);
+      if (k2 < lo.z) atomicMin(lo_p + 2, k2);
+      if (k3 < lo.w) atomicMin(lo_p + 3, k3);
+      if (k4 < hi.x) atomicMin(hi_p + 0, k4);
+      if (k5 < hi.y) atomicMin(hi_p + 1, k5);
+      if (k6 < hi.z) atomicMin(hi_p + 2, k6);
+      if (k7 < hi.w) atomicMin(hi_p + 3, k7);
+    }
+  };
+  uint4 x0[U], x1[U];
+  int32_t a0[U], o0[U], a1[U], o1[U];
+  int64_t b = R0 + rl;
+  load(b, x0, a0, o0);
+  for (; b < R1; b += 2 * 64 * U) {
+    load(b + 64 * U, x1, a1, o1);
+    fold(b, x0, a0, o0);
+    load(b + 2 * 64 * U, x0, a0, o0);
+    fold(b + 64 * U, x1, a1, o1);
+  }
+  __syncthreads();
+  uint32_t* out = part + (int64_t)r * k * k;
+  for (int i = tid; i < k * kStreamCols; i += kThreads) {
+    const int u = i / kStreamCols, pc = i % kStreamCols;
+    const int col = pc < 32 ? 8 * (pc >> 2) + (pc & 3) : 8 * ((pc - 32) >> 2) + 4 + (pc & 3);
+    if (col < w) out[(int64_t)u * k + c0 + col] = acc[i];
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) bt_merge_ranges(const uint32_t* __restrict__ part,
+                                                            int nranges, int32_t n, int32_t k,
+                                                            int32_t* tc, int32_t* td) {
+  const int64_t kk = (int64_t)k * k;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < kk;
+       i += (int64_t)gridDim.x * kThreads) {
+    uint32_t best = 0xffffffffu;
+    int br = -1;
+    for (int r = 0; r < nranges; ++r) {
+      const uint32_t key = part[r * kk + i];
+      if (key != 0xffffffffu && (br < 0 || (key >> 16) < (best >> 16))) { best = key; br = r; }
+    }
+    const int32_t u = (int32_t)(i / k), v = (int32_t)(i % k);
+    if (br < 0 || u == v) {
+      tc[i] = kTInf;
+      td[i] = -1;
+    } else {
+      tc[i] = (int32_t)(best >> 16) - 32768;
+      td[i] = (int32_t)((int64_t)br * n / nranges + (best & 0xffffu));
+    }
+  }
+}
+
 int bt_max_k(int elem_bytes) { return kThreads * (16 / elem_bytes); }
 
 // Sets the bulk scan's dynamic shared memory limit once per device.
@@ -749,6 +905,27 @@ cudaError_t best_transfer_run(int32_t n, int32_t k, const void* cm, int elem_byt
                               cudaStream_t st, int num_sms) {
   void* base = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
   const BtWorkspace W = carve(base, n, k);
+  const int nranges = elem_bytes == 2 ? stream_ranges(n, k, num_sms) : 0;
+  if (nranges > 0) {
+    static std::atomic<uint64_t> attr_set{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!(attr_set.load() & (1ull << dev))) {
+      e = cudaFuncSetAttribute(bt_scan_stream16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               4 * kStreamMaxK * kStreamCols);
+      if (e != cudaSuccess) return e;
+      attr_set.fetch_or(1ull << dev);
+    }
+    const int16_t* cm16 = static_cast<const int16_t*>(cm);
+    const int nslice = (k + kStreamCols - 1) / kStreamCols;
+    bt_own<<<num_sms * 4, kThreads, 0, st>>>(assign, n, k, cm16, ld, W.perm);
+    bt_scan_stream16<<<nslice * nranges, kThreads, 4 * (size_t)k * kStreamCols, st>>>(
+        cm16, ld, n, k, assign, W.perm, nslice, nranges, W.part);
+    bt_merge_ranges<<<num_sms * 4, kThreads, 0, st>>>(W.part, nranges, n, k, tc, td);
+    return cudaGetLastError();
+  }
   cudaError_t e = cudaMemsetAsync(W.ctl, 0, 4 * BT_CTL_WORDS + 4ull * (k + 1), st);
   if (e != cudaSuccess) return e;
   bt_count<<<kTiles, kTileThreads, 4 * (size_t)k, st>>>(assign, n, k, W.cnt, W.tile_rel);
