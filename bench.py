@@ -383,7 +383,7 @@ def run_ours(args):
     steps = args.steps
     w = st1.cm_elem_bytes
     rows_full = (dstat("rows_scanned") + 2 * inst.n * steps)     # rescans + prologue + merges
-    alg_bytes = (rows_full * inst.k * w + dstat("col_rows") * 2 * w) / steps
+    alg_bytes = (rows_full * inst.k * w + dstat("col_rows") * (w + 4)) / steps
     achieved = alg_bytes / (ms_per_step / 1000.0) / 1e9
     # the committed figure is for whole solves of its own workload
     traffic = (committed_traffic("asral_cluster_kernel", args.workload)
@@ -731,17 +731,36 @@ def run_large(args):
         del buf, cm2, assign, tc, td
         torch.cuda.empty_cache()
     assert scans["i16"]["table_sha256"] == scans["i32"]["table_sha256"]
-    # solver prefix
+    # solver prefix: the first rounds of the stored oracle prefix are checked
+    # (allotment, loads and objective digests), then the prefix goes on to
+    # `large_rounds`; both parts are timed
+    with open(os.path.join(ROOT, "tests", "golden", "large_r9000_oracle.json")) as f:
+        gold = json.load(f)
     solver = lb.Solver(inst.cm, inst.cap, inst.pen)
     solver.solve(0)                      # prologue (s_min and the MinDistance order)
     torch.cuda.synchronize()
     e0, e1 = _events()
+    first = min(args.large_rounds, gold["rounds"])
     e0.record()
-    solver.solve(args.large_rounds)
+    solver.solve(first)
     e1.record()
     torch.cuda.synchronize()
-    clk = clocks.stop()
     ms = e0.elapsed_time(e1)
+    check = None
+    if first == gold["rounds"]:
+        sha = lambda a: hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+        st0 = solver.stats()
+        check = {"rounds": first, "objective_equals_oracle": solver.objective == gold["delta"],
+                 "assignment_equal": sha(solver.assignment().astype(np.int32)) == gold["assign_sha256"],
+                 "loads_equal": sha(solver.loads().astype(np.int64)) == gold["load_sha256"],
+                 "moves": st0.moves, "oracle_moves": gold["stats"]["moves"]}
+    if args.large_rounds > first:
+        e0.record()
+        solver.solve(args.large_rounds)
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    clk = clocks.stop()
     st = solver.stats()
     rounds = solver.rounds
     solver.close()
@@ -758,9 +777,11 @@ def run_large(args):
                      "frac": scans["i16"]["frac"], "peak_kind": peak_kind, "traffic": None},
         "scan": scans,
         "solver_prefix": {"rounds": rounds, "ms": ms, "rounds_per_s": rounds / (ms / 1000.0),
+                          "us_per_round": 1000.0 * ms / max(1, rounds),
                           "bf_sweeps_per_round": st.bf_sweeps / max(1, rounds),
-                          "cluster_size": st.cluster_size},
-        "gpu_launches": 2 * 20 * 10 + 1, "clocks": clk,
+                          "cycles_applied": st.cycles_applied, "paths_applied": st.paths_applied,
+                          "cluster_size": st.cluster_size, "oracle_prefix_check": check},
+        "gpu_launches": 2 * 20 * 6 + 2, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
 
@@ -1090,7 +1111,7 @@ def city_measure(lb, hbm_peak, peak_kind):
     with open(os.path.join(ROOT, "tests", "golden", "city_oracle.json")) as f:
         gold = json.load(f)
     w = st.cm_elem_bytes
-    alg = (st.rows_scanned + 2 * inst.n) * inst.k * w + st.col_rows * 2 * w
+    alg = (st.rows_scanned + 2 * inst.n) * inst.k * w + st.col_rows * (w + 4)
     achieved = alg / (ms / 1000.0) / 1e9
     traffic = committed_traffic("asral_cluster_kernel", "city")
     roof = {"kernel": "asral_cluster_kernel", "bound": "hbm", "achieved": achieved,

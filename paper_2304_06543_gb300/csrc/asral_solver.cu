@@ -164,7 +164,7 @@ struct Solver {
   int buf;            // exchange buffer parity, advances every sweep
 
   Book* B;            // CTA 0 thread 0 bookkeeping (shared memory)
-  int32_t pending_d = -1, pending_j = -1;
+  int32_t pending_d = -1, pending_j = -1, pending_own = 0;
 
   // Phase timers run on CTA 0's thread 0, on the path every other CTA waits
   // for at the cluster barriers, so they are off unless asked for.
@@ -173,9 +173,11 @@ struct Solver {
   }
   __device__ __forceinline__ const T* row(int32_t d) const { return cm + (int64_t)d * I.ld; }
 
+  // Member idx of c's list; the member's own cost CM(d, c) sits kPage
+  // words further in the same page, so rescans need no CM read for it.
   __device__ __forceinline__ int32_t* mslot(int32_t c, int32_t idx) const {
     int32_t page = __ldcg(I.page_tab + (int64_t)c * I.max_pages + (idx >> kPageShift));
-    return I.pool + ((int64_t)page << kPageShift) + (idx & (kPage - 1));
+    return I.pool + (int64_t)page * kPageWords + (idx & (kPage - 1));
   }
 
   // Owned cost of row u, owned column cl (kTInf for "no edge").
@@ -192,8 +194,9 @@ struct Solver {
     if (tsm_on) s_tc[u * ws + cl] = (TS)(t == kTInf ? kTsInf : t);
   }
 
-  // Member-list primitives, called by one thread of CTA 0 only.
-  __device__ void list_append(int32_t c, int32_t d) {
+  // Member-list primitives, called by one thread of CTA 0 only.  `own` is
+  // CM(d, c).
+  __device__ void list_append(int32_t c, int32_t d, int32_t own) {
     int32_t idx = I.seg_size[c];
     if (c < 0 || c >= k || d < 0 || d >= n || idx < 0 || idx >= n) { B->err0 = ST_ERR_INVARIANT; return; }
     if ((idx & (kPage - 1)) == 0) {
@@ -201,7 +204,9 @@ struct Solver {
       int32_t page = I.free_stack[--B->free_top];
       I.page_tab[(int64_t)c * I.max_pages + (idx >> kPageShift)] = page;
     }
-    *mslot(c, idx) = d;
+    int32_t* slot = mslot(c, idx);
+    slot[0] = d;
+    slot[kPage] = own;
     I.pos[d] = idx;
     I.seg_size[c] = idx + 1;
   }
@@ -214,8 +219,11 @@ struct Solver {
       return;
     }
     if (idx != last) {
-      int32_t moved = *mslot(c, last);
-      *mslot(c, idx) = moved;
+      const int32_t* from = mslot(c, last);
+      int32_t* to = mslot(c, idx);
+      const int32_t moved = from[0];
+      to[0] = moved;
+      to[kPage] = from[kPage];
       I.pos[moved] = idx;
     }
     if ((last & (kPage - 1)) == 0)
@@ -429,23 +437,19 @@ struct Solver {
     for (int q = 0; q < VPL; ++q) { bt[q] = kTInf; bd[q] = -1; }
     if (g < R) {
       for (int32_t base = g; base < s; base += U * R) {
-        int32_t dd[U];
+        int32_t dd[U], own[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int32_t idx = base + u * R;
-          dd[u] = idx < s ? __ldcg(mslot(c, idx)) : -1;
+          const int32_t* sl = idx < s ? mslot(c, idx) : nullptr;
+          dd[u] = sl ? __ldcg(sl) : -1;
+          own[u] = sl ? __ldcg(sl + kPage) : 0;
           if ((uint32_t)dd[u] >= (uint32_t)n) dd[u] = -1;   // guard: corrupt entry
         }
-        int32_t own[U];
         Vec16<T> x[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (dd[u] >= 0) {
-            const T* r = row(dd[u]);
-            own[u] = (int32_t)r[c];
-            x[u] = load16(r + c0 + slot * VPL);
-          }
-        }
+        for (int u = 0; u < U; ++u)
+          if (dd[u] >= 0) x[u] = load16(row(dd[u]) + c0 + slot * VPL);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (dd[u] < 0) continue;
@@ -1180,7 +1184,9 @@ struct Solver {
         const int32_t x_out = s_pathu[i];
         const int32_t x_in = (i > 0) ? s_pathu[i - 1] : (npath ? -1 : s_pathu[m - 1]);
         if (x_out >= 0 && x_in >= 0 && ppos[i] >= 0 && ppos[i] < n) {
-          *mslot(c, ppos[i]) = x_in;
+          int32_t* slot = mslot(c, ppos[i]);
+          slot[0] = x_in;
+          slot[kPage] = (int32_t)row(x_in)[c];
           I.pos[x_in] = ppos[i];
         }
         if (x_out >= 0) I.assign[x_out] = (i + 1 < m) ? s_path[i + 1] : j;
@@ -1196,7 +1202,7 @@ struct Solver {
             list_remove_at(c, ppos[i]);
             I.load[c] -= 1;
           } else if (x_out < 0 && x_in >= 0) {
-            list_append(c, x_in);
+            list_append(c, x_in, (int32_t)row(x_in)[c]);
             I.load[c] += 1;
           }
         }
@@ -1205,7 +1211,8 @@ struct Solver {
         if (npath) {
           // the anchor loses x_0, the terminal center gains x_{m-2}
           list_remove_at(j, ppos[0]);
-          if (s_pathu[m - 2] >= 0) list_append(s_path[m - 1], s_pathu[m - 2]);
+          if (s_pathu[m - 2] >= 0)
+            list_append(s_path[m - 1], s_pathu[m - 2], (int32_t)row(s_pathu[m - 2])[s_path[m - 1]]);
           else B->err0 = ST_ERR_INVARIANT;
           I.load[j] -= 1;
           I.load[s_path[m - 1]] += 1;
@@ -1289,18 +1296,19 @@ struct Solver {
       unsigned long long best = ~0ull;
       constexpr int U = 4;
       for (int32_t base = i0; base < s; base += U * stride) {
-        int32_t dd[U];
+        int32_t dd[U], own[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int32_t idx = base + u * stride;
-          dd[u] = idx < s ? __ldcg(mslot(c, idx)) : -1;
+          const int32_t* sl = idx < s ? mslot(c, idx) : nullptr;
+          dd[u] = sl ? __ldcg(sl) : -1;
+          own[u] = sl ? __ldcg(sl + kPage) : 0;
           if ((uint32_t)dd[u] >= (uint32_t)n) dd[u] = -1;   // guard: corrupt entry
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (dd[u] < 0) continue;
-          const T* r = row(dd[u]);
-          const int32_t t = (int32_t)r[v] - (int32_t)r[c];
+          const int32_t t = (int32_t)row(dd[u])[v] - own[u];
           const unsigned long long key =
               ((unsigned long long)(uint32_t)(t + (int64_t)2147483648LL) << 32) | (uint32_t)dd[u];
           best = min(best, key);
@@ -1376,7 +1384,8 @@ struct Solver {
         // Member lists are touched only after the next cluster barrier (the
         // first Bellman-Ford sweep), when every CTA has finished reading
         // them for the previous round's rescans.
-        B->delta += (int64_t)row(d)[j] + q_over;
+        pending_own = (int32_t)row(d)[j];
+        B->delta += (int64_t)pending_own + q_over;
         if (timer()) B->t_merge += clock_cycles() - tm0;
       }
       __syncthreads();
@@ -1446,7 +1455,7 @@ struct Solver {
     if (pending_d >= 0) {
       if (rank == 0 && tid == 0) {
         I.assign[pending_d] = pending_j;
-        list_append(pending_j, pending_d);
+        list_append(pending_j, pending_d, pending_own);
         I.load[pending_j] += 1;
       }
       pending_d = -1;

@@ -228,7 +228,7 @@ size_t lbdd::solver_footprint(int32_t n, int32_t k, int in_elem, int elem) {
   b += 2 * a(4ull * n) + a(12ull * n);        // smin, order, sort_tmp
   b += 2 * a(4ull * n);                       // assign, pos
   b += 2 * a(4ull * k);                       // load, seg_size
-  b += a(4ull * k * max_pages) + a(4ull * npages * kPage) + a(4ull * npages);
+  b += a(4ull * k * max_pages) + a(4ull * npages * kPageWords) + a(4ull * npages);
   b += 2 * a(4ull * k * k);                   // tc, td
   b += a(8ull * CTL_COUNT) + a(16) + a(sizeof(DevInst));
   return b;
@@ -268,7 +268,7 @@ static int create_impl(lbdd_solver** out, int32_t n, int32_t k, const void* cm, 
   if (!rc) rc = dalloc(s, &s->load, k);
   if (!rc) rc = dalloc(s, &s->seg_size, k);
   if (!rc) rc = dalloc(s, &s->page_tab, (size_t)k * max_pages);
-  if (!rc) rc = dalloc(s, &s->pool, (size_t)npages * kPage);
+  if (!rc) rc = dalloc(s, &s->pool, (size_t)npages * kPageWords);
   if (!rc) rc = dalloc(s, &s->free_stack, npages);
   if (!rc) rc = dalloc(s, &s->tc, (size_t)k * k);
   if (!rc) rc = dalloc(s, &s->td, (size_t)k * k);
@@ -291,7 +291,7 @@ static int create_impl(lbdd_solver** out, int32_t n, int32_t k, const void* cm, 
   if ((e = cudaMemsetAsync(s->load, 0, 4ull * k, s->st))) return fail(e, "load");
   // defined contents everywhere, so that a corrupt index can never leave the pool
   if ((e = cudaMemsetAsync(s->page_tab, 0, 4ull * k * max_pages, s->st))) return fail(e, "pages");
-  if ((e = cudaMemsetAsync(s->pool, 0, 4ull * npages * kPage, s->st))) return fail(e, "pool");
+  if ((e = cudaMemsetAsync(s->pool, 0, 4ull * npages * kPageWords, s->st))) return fail(e, "pool");
   if ((e = cudaMemsetAsync(s->pos, 0, 4ull * n, s->st))) return fail(e, "pos");
   if ((e = cudaMemcpyAsync(s->d_inst, &I, sizeof(DevInst), cudaMemcpyHostToDevice, s->st))) return fail(e, "inst");
   if ((e = cudaStreamSynchronize(s->st))) return fail(e, "sync");
@@ -601,7 +601,7 @@ static int grow_units(lbdd_solver* s, int32_t cap_new) {
   if (!rc) rc = dalloc(s, &assign, cap_new);
   if (!rc) rc = dalloc(s, &pos, cap_new);
   if (!rc) rc = dalloc(s, &page_tab, (size_t)k * mp_new);
-  if (!rc) rc = dalloc(s, &pool, (size_t)np_new * kPage);
+  if (!rc) rc = dalloc(s, &pool, (size_t)np_new * kPageWords);
   if (!rc) rc = dalloc(s, &free_stack, np_new);
   if (rc) {   // the solver keeps its old arrays
     for (void* p : {cm, (void*)smin, (void*)order, (void*)sort_tmp, (void*)assign, (void*)pos,
@@ -621,8 +621,8 @@ static int grow_units(lbdd_solver* s, int32_t cap_new) {
   CK(cudaMemsetAsync(page_tab, 0, 4ull * k * mp_new, s->st));
   CK(cudaMemcpy2DAsync(page_tab, 4ull * mp_new, s->page_tab, 4ull * mp_old, 4ull * mp_old, k, dd,
                        s->st));
-  CK(cudaMemsetAsync(pool, 0, 4ull * np_new * kPage, s->st));
-  CK(cudaMemcpyAsync(pool, s->pool, 4ull * np_old * kPage, dd, s->st));
+  CK(cudaMemsetAsync(pool, 0, 4ull * np_new * kPageWords, s->st));
+  CK(cudaMemcpyAsync(pool, s->pool, 4ull * np_old * kPageWords, dd, s->st));
   CK(cudaMemcpyAsync(free_stack, s->free_stack, 4ull * np_old, dd, s->st));
   int64_t h[2];
   CK(cudaMemcpyAsync(h, s->ctl + CTL_PROLOGUE, sizeof(int64_t), cudaMemcpyDeviceToHost, s->st));

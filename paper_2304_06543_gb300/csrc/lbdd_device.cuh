@@ -13,6 +13,7 @@ constexpr int kThreads = 512;          // threads per CTA of every kernel here
 constexpr int kWarps = kThreads / 32;
 constexpr int kPageShift = 8;          // member lists are paged, 256 units/page
 constexpr int kPage = 1 << kPageShift;
+constexpr int kPageWords = 2 * kPage;  // a page: kPage unit ids, then their own costs CM(d, c)
 constexpr int kMaxCluster = 16;        // cluster sizes 1..16 (16 is non-portable)
 constexpr int32_t kTInf = INT32_MAX;   // best-transfer entry of an empty segment
 constexpr int64_t kDInf = (int64_t)1 << 62;  // unreached Bellman-Ford label
@@ -88,7 +89,7 @@ struct DevInst {
   int32_t* load;        // k: units allotted per center
   int32_t* seg_size;    // k: length of each member list
   int32_t* page_tab;    // k x max_pages: page ids of each member list
-  int32_t* pool;        // pages x kPage member slots
+  int32_t* pool;        // pages x kPageWords: member ids, then each member's own cost
   int32_t* free_stack;  // pages
   int32_t* tc;          // k x k best-transfer cost (row u = from u)
   int32_t* td;          // k x k best-transfer unit
