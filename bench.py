@@ -56,7 +56,11 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["headline", "city", "tiny", "batch", "serve", "large",
-                                           "road"], default="headline")
+                                           "road", "scan"], default="headline")
+    ap.add_argument("--scan-of", choices=["city", "large"], default="city",
+                    help="scan: the instance whose s_min table is computed")
+    ap.add_argument("--scan-n", type=int, default=0,
+                    help="scan: demand units of that instance (0 = its stated size)")
     ap.add_argument("--per-step", type=int, default=4,
                     help="headline: serving-stream requests per step")
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
@@ -1085,6 +1089,40 @@ def scan_measure(lb, hbm_peak, peak_kind, reps: int = 20):
     return out
 
 
+def run_scan(args):
+    """The full best-transfer table alone: the s_min allotment of the city or
+    the large instance (optionally with fewer units), int16 and int32, `steps`
+    calls after 3 warm-ups each, whole-call device time."""
+    import torch
+    import lbdd_inputs as L
+    import paper_2304_06543_gb300 as lb
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    lb.load()
+    hbm_peak, peak_kind = peaks()
+    over = {"n": args.scan_n} if args.scan_n > 0 else {}
+    inst = L.make_named(args.scan_of, dtype="i16", **over)
+    clocks = ClockSampler(local)
+    clocks.start()
+    res = {dt: _scan_case(lb, inst.cm, dt, hbm_peak, peak_kind, args.steps) for dt in ("i16", "i32")}
+    clk = clocks.stop()
+    line = {
+        "metric": "scan GB/s vs HBM", "value": res["i16"]["achieved"], "unit": "GB/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": 3, "ms_per_step": res["i16"]["ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int16",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": f"best-transfer table of the s_min allotment of the {args.scan_of} "
+                               f"instance, {inst.n} x {inst.k}", "n": inst.n, "k": inst.k},
+        "roofline": res["i16"], "scan": res,
+        "tables_equal_i16_i32": res["i16"]["table_sha256"] == res["i32"]["table_sha256"],
+        # per call: bt_own, bt_scan_stream16, bt_merge_ranges on the int16 row-order path,
+        # else bt_count, bt_plan, bt_place, bt_sort_items, the scan and bt_unpack
+        "gpu_launches": args.steps * ((3 if 256 <= inst.k <= 512 and inst.n <= 32 * 65536 else 6) + 6),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def city_measure(lb, hbm_peak, peak_kind):
     """One whole solve of the 200,000 x 500 city instance (a single persistent
     launch), its objective against the stored whole-solve oracle result, and
@@ -1368,6 +1406,8 @@ def main():
         run_large(args)
     elif args.workload == "road":
         run_road(args)
+    elif args.workload == "scan":
+        run_scan(args)
     else:
         run_ours(args)
 
