@@ -737,8 +737,10 @@ __global__ void __launch_bounds__(kThreads) bt_unpack(const unsigned long long* 
 // r, and keeps in shared memory one 32-bit key per (center, column of the
 // slice): ((t + 32768) << 16) | (d - first row of the range), so the smaller
 // key is the lexicographically smaller (t, d) inside the range.  A thread
-// reads 16 bytes (8 columns) of kStreamUnroll rows at once, compares its keys
-// with the table and lowers an entry with a shared atomicMin only where its
+// owns 16 bytes (8 columns) of every 64th row; each is copied into the
+// thread's own shared slot by cp.async kStreamStages rows ahead (the bytes in
+// flight are bounded by shared memory, not registers), then the thread
+// compares its keys with the table and lowers an entry with a shared atomicMin only where its
 // key is smaller (entries only decrease, so a stale read never hides a
 // smaller key).  A table row is laid out as two halves: the first 4 columns
 // of every thread's 8 at words 4 * cg, the other 4 at 32 + 4 * cg, so each
@@ -746,7 +748,20 @@ __global__ void __launch_bounds__(kThreads) bt_unpack(const unsigned long long* 
 // CM(d, assign[d]) first; bt_merge_ranges takes, for every (u, v), the
 // smallest t over the ranges in range order (ranges ascend in d, so the first
 // range that attains it holds the smallest d) and writes tc/td.
-constexpr int kStreamUnroll = 6;
+constexpr int kStreamStages = 11;       // rows in flight per thread (cp.async stages)
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Dynamic shared memory of bt_scan_stream16: the key table, then the stages.
+static size_t stream_smem_bytes(int32_t k) {
+  return 4 * (size_t)k * kStreamCols + (size_t)kStreamStages * kThreads * 16;
+}
 
 // Row ranges of the row-order path on `num_sms` SMs, 0 if it does not apply.
 static int stream_ranges(int32_t n, int32_t k, int num_sms) {
@@ -774,8 +789,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 bt_scan_stream16(const int16_t* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
                  const int32_t* __restrict__ assign, const int32_t* __restrict__ own, int nslice,
                  int nranges, uint32_t* part) {
-  constexpr int U = kStreamUnroll;
-  extern __shared__ __align__(16) uint32_t acc[];   // k rows of kStreamCols keys
+  constexpr int P = kStreamStages;
+  extern __shared__ __align__(16) uint32_t acc[];   // k rows of kStreamCols keys, then the stages
   const int tid = threadIdx.x, cg = tid & 7, rl = tid >> 3;
   const int j = blockIdx.x % nslice, r = blockIdx.x / nslice;
   const int64_t R0 = (int64_t)r * n / nranges, R1 = (int64_t)(r + 1) * n / nranges;
@@ -786,52 +801,66 @@ bt_scan_stream16(const int16_t* __restrict__ cm, int64_t ld, int32_t n, int32_t 
   for (int i = tid; i < k * kStreamCols / 4; i += kThreads) reinterpret_cast<uint4*>(acc)[i] = none;
   __syncthreads();
   const int16_t* colp = cm + c0 + cg * 8;
-  // two register batches of U rows: the next batch's loads are in flight
-  // while the current one is compared
-  auto load = [&](int64_t b, uint4* x, int32_t* a, int32_t* o) {
+  // rows of this thread: R0 + rl + 64 i, i < M; row i's 16 bytes go to
+  // stage i % P of the thread's own shared slots P rows ahead (cp.async: a
+  // thread waits only for its own copies, no barrier), its center and own
+  // cost to a register ring P rows ahead
+  const int64_t span = R1 - R0;
+  const int32_t M = act && rl < span ? (int32_t)((span - rl + 63) / 64) : 0;
+  uint4* stage = reinterpret_cast<uint4*>(acc + k * kStreamCols);   // [P][kThreads]
+  int32_t ra[P], ro[P];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t d = b + 64 * u;
-      const bool v = d < R1;
-      a[u] = v ? __ldg(assign + d) : -1;
-      o[u] = v ? __ldg(own + d) : 0;
-      x[u] = (v && act) ? __ldg(reinterpret_cast<const uint4*>(colp + d * ld)) : make_uint4(0, 0, 0, 0);
+  for (int q = 0; q < P; ++q) {
+    const int64_t d = R0 + rl + 64 * q;
+    ra[q] = -1;
+    ro[q] = 0;
+    if (q < M) {
+      cp_async16(&stage[q * kThreads + tid], colp + d * ld);
+      ra[q] = __ldg(assign + d);
+      ro[q] = __ldg(own + d);
     }
-  };
-  auto fold = [&](int64_t b, const uint4* x, const int32_t* a, const int32_t* o) {
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (!act || a[u] < 0 || a[u] >= k) continue;
-      const uint32_t crow = ((uint32_t)(32768 - o[u]) << 16) | (uint32_t)(b + 64 * u - R0);
-      uint32_t* row = acc + a[u] * kStreamCols;
-      uint32_t* lo_p = row + 4 * cg;
-      uint32_t* hi_p = row + 32 + 4 * cg;
-      const uint4 lo = *reinterpret_cast<const uint4*>(lo_p);
-      const uint4 hi = *reinterpret_cast<const uint4*>(hi_p);
-      const uint32_t k0 = (x[u].x << 16) + crow, k1 = (x[u].x & 0xffff0000u) + crow;
-      const uint32_t k2 = (x[u].y << 16) + crow, k3 = (x[u].y & 0xffff0000u) + crow;
-      const uint32_t k4 = (x[u].z << 16) + crow, k5 = (x[u].z & 0xffff0000u) + crow;
-      const uint32_t k6 = (x[u].w << 16) + crow, k7 = (x[u].w & 0xffff0000u) + crow;
-      if (k0 < lo.x) atomicMin(lo_p + 0, k0);
-      if (k1 < lo.y) atomicMin(lo_p + 1, k1);
-      if (k2 < lo.z) atomicMin(lo_p + 2, k2);
-      if (k3 < lo.w) atomicMin(lo_p + 3, k3);
-      if (k4 < hi.x) atomicMin(hi_p + 0, k4);
-      if (k5 < hi.y) atomicMin(hi_p + 1, k5);
-      if (k6 < hi.z) atomicMin(hi_p + 2, k6);
-      if (k7 < hi.w) atomicMin(hi_p + 3, k7);
-    }
-  };
-  uint4 x0[U], x1[U];
-  int32_t a0[U], o0[U], a1[U], o1[U];
-  int64_t b = R0 + rl;
-  load(b, x0, a0, o0);
-  for (; b < R1; b += 2 * 64 * U) {
-    load(b + 64 * U, x1, a1, o1);
-    fold(b, x0, a0, o0);
-    load(b + 2 * 64 * U, x0, a0, o0);
-    fold(b + 64 * U, x1, a1, o1);
+    cp_async_commit();
   }
+  for (int32_t m = 0; m < M; m += P) {
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      cp_async_wait<P - 1>();                      // row m + q has landed
+      const int32_t a = ra[q], o = ro[q];
+      const int32_t i = m + q;
+      if (i < M && a >= 0 && a < k) {
+        const uint4 x = stage[q * kThreads + tid];
+        const uint32_t crow = ((uint32_t)(32768 - o) << 16) | (uint32_t)(rl + 64 * i);
+        uint32_t* row = acc + a * kStreamCols;
+        uint32_t* lo_p = row + 4 * cg;
+        uint32_t* hi_p = row + 32 + 4 * cg;
+        const uint4 lo = *reinterpret_cast<const uint4*>(lo_p);
+        const uint4 hi = *reinterpret_cast<const uint4*>(hi_p);
+        const uint32_t k0 = (x.x << 16) + crow, k1 = (x.x & 0xffff0000u) + crow;
+        const uint32_t k2 = (x.y << 16) + crow, k3 = (x.y & 0xffff0000u) + crow;
+        const uint32_t k4 = (x.z << 16) + crow, k5 = (x.z & 0xffff0000u) + crow;
+        const uint32_t k6 = (x.w << 16) + crow, k7 = (x.w & 0xffff0000u) + crow;
+        if (k0 < lo.x) atomicMin(lo_p + 0, k0);
+        if (k1 < lo.y) atomicMin(lo_p + 1, k1);
+        if (k2 < lo.z) atomicMin(lo_p + 2, k2);
+        if (k3 < lo.w) atomicMin(lo_p + 3, k3);
+        if (k4 < hi.x) atomicMin(hi_p + 0, k4);
+        if (k5 < hi.y) atomicMin(hi_p + 1, k5);
+        if (k6 < hi.z) atomicMin(hi_p + 2, k6);
+        if (k7 < hi.w) atomicMin(hi_p + 3, k7);
+      }
+      // stage q now takes row i + P
+      const int32_t nx = i + P;
+      ra[q] = -1;
+      if (nx < M) {
+        const int64_t d = R0 + rl + 64 * (int64_t)nx;
+        cp_async16(&stage[q * kThreads + tid], colp + d * ld);
+        ra[q] = __ldg(assign + d);
+        ro[q] = __ldg(own + d);
+      }
+      cp_async_commit();
+    }
+  }
+  cp_async_wait<0>();
   __syncthreads();
   uint32_t* out = part + (int64_t)r * k * k;
   for (int i = tid; i < k * kStreamCols; i += kThreads) {
@@ -914,14 +943,14 @@ cudaError_t best_transfer_run(int32_t n, int32_t k, const void* cm, int elem_byt
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!(attr_set.load() & (1ull << dev))) {
       e = cudaFuncSetAttribute(bt_scan_stream16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               4 * kStreamMaxK * kStreamCols);
+                               (int)stream_smem_bytes(kStreamMaxK));
       if (e != cudaSuccess) return e;
       attr_set.fetch_or(1ull << dev);
     }
     const int16_t* cm16 = static_cast<const int16_t*>(cm);
     const int nslice = (k + kStreamCols - 1) / kStreamCols;
     bt_own<<<num_sms * 4, kThreads, 0, st>>>(assign, n, k, cm16, ld, W.perm);
-    bt_scan_stream16<<<nslice * nranges, kThreads, 4 * (size_t)k * kStreamCols, st>>>(
+    bt_scan_stream16<<<nslice * nranges, kThreads, stream_smem_bytes(k), st>>>(
         cm16, ld, n, k, assign, W.perm, nslice, nranges, W.part);
     bt_merge_ranges<<<num_sms * 4, kThreads, 0, st>>>(W.part, nranges, n, k, tc, td);
     return cudaGetLastError();
