@@ -118,3 +118,16 @@ def test_default_arguments():
     a = bench.parse([])
     assert (a.workload, a.steps, a.per_step, a.large) == ("headline", 20, 4, "100000x1000")
     assert a.warmup >= 3
+
+
+def test_scan_workload_arguments_and_reference_arm():
+    a = bench.parse(["--workload", "scan", "--scan-of", "large", "--scan-n", "200000"])
+    assert (a.workload, a.scan_of, a.scan_n) == ("scan", "large", 200000)
+    b = bench.parse(["--workload", "scan"])
+    assert (b.scan_of, b.scan_n) == ("city", 0)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "scan", "--steps", "1", "--warmup", "3"],
+                         capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and "unavailable" in d
