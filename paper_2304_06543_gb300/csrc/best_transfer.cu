@@ -737,7 +737,7 @@ __global__ void __launch_bounds__(kThreads) bt_unpack(const unsigned long long* 
 // r, and keeps in shared memory one 32-bit key per (center, column of the
 // slice): ((t + 32768) << 16) | (d - first row of the range), so the smaller
 // key is the lexicographically smaller (t, d) inside the range.  A thread
-// owns 16 bytes (8 columns) of every 64th row; each is copied into the
+// owns 16 bytes (8 columns) of every 128th row; each is copied into the
 // thread's own shared slot by cp.async kStreamStages rows ahead (the bytes in
 // flight are bounded by shared memory, not registers), then the thread
 // compares its keys with the table and lowers an entry with a shared atomicMin only where its
@@ -748,7 +748,8 @@ __global__ void __launch_bounds__(kThreads) bt_unpack(const unsigned long long* 
 // CM(d, assign[d]) first; bt_merge_ranges takes, for every (u, v), the
 // smallest t over the ranges in range order (ranges ascend in d, so the first
 // range that attains it holds the smallest d) and writes tc/td.
-constexpr int kStreamStages = 11;       // rows in flight per thread (cp.async stages)
+constexpr int kStreamThreads = 1024;    // 8 threads per 128-byte row slice, 128 rows at a time
+constexpr int kStreamStages = 5;        // rows in flight per thread (cp.async stages)
 
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
   const uint32_t a = (uint32_t)__cvta_generic_to_shared(sdst);
@@ -760,7 +761,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // Dynamic shared memory of bt_scan_stream16: the key table, then the stages.
 static size_t stream_smem_bytes(int32_t k) {
-  return 4 * (size_t)k * kStreamCols + (size_t)kStreamStages * kThreads * 16;
+  return 4 * (size_t)k * kStreamCols + (size_t)kStreamStages * kStreamThreads * 16;
 }
 
 // Row ranges of the row-order path on `num_sms` SMs, 0 if it does not apply.
@@ -785,7 +786,7 @@ __global__ void __launch_bounds__(kThreads) bt_own(const int32_t* __restrict__ a
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kStreamThreads, 1)
 bt_scan_stream16(const int16_t* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
                  const int32_t* __restrict__ assign, const int32_t* __restrict__ own, int nslice,
                  int nranges, uint32_t* part) {
@@ -798,24 +799,24 @@ bt_scan_stream16(const int16_t* __restrict__ cm, int64_t ld, int32_t n, int32_t 
   const int w = min(kStreamCols, k - c0);
   const bool act = cg * 8 < w;
   const uint4 none = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-  for (int i = tid; i < k * kStreamCols / 4; i += kThreads) reinterpret_cast<uint4*>(acc)[i] = none;
+  for (int i = tid; i < k * kStreamCols / 4; i += kStreamThreads) reinterpret_cast<uint4*>(acc)[i] = none;
   __syncthreads();
   const int16_t* colp = cm + c0 + cg * 8;
-  // rows of this thread: R0 + rl + 64 i, i < M; row i's 16 bytes go to
+  // rows of this thread: R0 + rl + 128 i, i < M; row i's 16 bytes go to
   // stage i % P of the thread's own shared slots P rows ahead (cp.async: a
   // thread waits only for its own copies, no barrier), its center and own
   // cost to a register ring P rows ahead
   const int64_t span = R1 - R0;
-  const int32_t M = act && rl < span ? (int32_t)((span - rl + 63) / 64) : 0;
-  uint4* stage = reinterpret_cast<uint4*>(acc + k * kStreamCols);   // [P][kThreads]
+  const int32_t M = act && rl < span ? (int32_t)((span - rl + 127) / 128) : 0;
+  uint4* stage = reinterpret_cast<uint4*>(acc + k * kStreamCols);   // [P][kStreamThreads]
   int32_t ra[P], ro[P];
 #pragma unroll
   for (int q = 0; q < P; ++q) {
-    const int64_t d = R0 + rl + 64 * q;
+    const int64_t d = R0 + rl + 128 * q;
     ra[q] = -1;
     ro[q] = 0;
     if (q < M) {
-      cp_async16(&stage[q * kThreads + tid], colp + d * ld);
+      cp_async16(&stage[q * kStreamThreads + tid], colp + d * ld);
       ra[q] = __ldg(assign + d);
       ro[q] = __ldg(own + d);
     }
@@ -828,8 +829,8 @@ bt_scan_stream16(const int16_t* __restrict__ cm, int64_t ld, int32_t n, int32_t 
       const int32_t a = ra[q], o = ro[q];
       const int32_t i = m + q;
       if (i < M && a >= 0 && a < k) {
-        const uint4 x = stage[q * kThreads + tid];
-        const uint32_t crow = ((uint32_t)(32768 - o) << 16) | (uint32_t)(rl + 64 * i);
+        const uint4 x = stage[q * kStreamThreads + tid];
+        const uint32_t crow = ((uint32_t)(32768 - o) << 16) | (uint32_t)(rl + 128 * i);
         uint32_t* row = acc + a * kStreamCols;
         uint32_t* lo_p = row + 4 * cg;
         uint32_t* hi_p = row + 32 + 4 * cg;
@@ -852,8 +853,8 @@ bt_scan_stream16(const int16_t* __restrict__ cm, int64_t ld, int32_t n, int32_t 
       const int32_t nx = i + P;
       ra[q] = -1;
       if (nx < M) {
-        const int64_t d = R0 + rl + 64 * (int64_t)nx;
-        cp_async16(&stage[q * kThreads + tid], colp + d * ld);
+        const int64_t d = R0 + rl + 128 * (int64_t)nx;
+        cp_async16(&stage[q * kStreamThreads + tid], colp + d * ld);
         ra[q] = __ldg(assign + d);
         ro[q] = __ldg(own + d);
       }
@@ -863,7 +864,7 @@ bt_scan_stream16(const int16_t* __restrict__ cm, int64_t ld, int32_t n, int32_t 
   cp_async_wait<0>();
   __syncthreads();
   uint32_t* out = part + (int64_t)r * k * k;
-  for (int i = tid; i < k * kStreamCols; i += kThreads) {
+  for (int i = tid; i < k * kStreamCols; i += kStreamThreads) {
     const int u = i / kStreamCols, pc = i % kStreamCols;
     const int col = pc < 32 ? 8 * (pc >> 2) + (pc & 3) : 8 * ((pc - 32) >> 2) + 4 + (pc & 3);
     if (col < w) out[(int64_t)u * k + c0 + col] = acc[i];
@@ -950,7 +951,7 @@ cudaError_t best_transfer_run(int32_t n, int32_t k, const void* cm, int elem_byt
     const int16_t* cm16 = static_cast<const int16_t*>(cm);
     const int nslice = (k + kStreamCols - 1) / kStreamCols;
     bt_own<<<num_sms * 4, kThreads, 0, st>>>(assign, n, k, cm16, ld, W.perm);
-    bt_scan_stream16<<<nslice * nranges, kThreads, stream_smem_bytes(k), st>>>(
+    bt_scan_stream16<<<nslice * nranges, kStreamThreads, stream_smem_bytes(k), st>>>(
         cm16, ld, n, k, assign, W.perm, nslice, nranges, W.part);
     bt_merge_ranges<<<num_sms * 4, kThreads, 0, st>>>(W.part, nranges, n, k, tc, td);
     return cudaGetLastError();
