@@ -30,11 +30,11 @@
 // Step 5 reads every CM byte of the allotted rows once and is the HBM-bound
 // kernel; the other steps move O(n + k*k) bytes.
 //
-// int16 costs with 256 to 512 centers take a shorter path with no grouping
-// (rows of 512 bytes to 1 KB gather poorly): bt_own, then bt_scan_stream16
-// reads the CM in row order, one 64-column slice and one row range per CTA,
-// keeping the minima in shared memory, and bt_merge_ranges combines the
-// ranges into (tc, td).
+// Tables of 256 to 512 centers take a shorter path with no grouping (rows of
+// 512 bytes to 2 KB gather poorly): bt_own, then bt_scan_stream reads the CM
+// in row order, one 128-byte column slice and one row range per CTA, keeping
+// the minima in shared memory, and bt_merge_ranges combines the ranges into
+// (tc, td).
 #include <atomic>
 #include <algorithm>
 
@@ -60,13 +60,14 @@ struct BtWorkspace {
   int32_t* perm;                // n (+ 4 readable): allotted units grouped by center
   int4* items;                  // n / kChunkMin + k + 1 items {center, first row, rows, 0}
   unsigned long long* t64;      // k x k packed ((cost + 2^31) << 32) | d
-  uint32_t* part;               // row-order int16 path: one k x k key table per row range
+  uint32_t* part;               // row-order path: one k x k key table per row range
   size_t bytes;
 };
 
-// Row-order int16 path (bt_scan_stream16): centers in [kStreamMinK,
-// kStreamMaxK], at most kStreamMaxRanges row ranges of at most
-// kStreamRowSpan rows each.
+// Row-order path (bt_scan_stream): centers in [kStreamMinK, kStreamMaxK];
+// int16: at most kStreamMaxRanges row ranges of at most kStreamRowSpan rows,
+// int32: at most kStreamMaxRanges / 2 ranges (twice as wide keys, the same
+// bytes of partial tables).
 constexpr int kStreamMinK = 256, kStreamMaxK = 512;
 constexpr int kStreamCols = 64;          // columns per slice: 128 bytes of a row
 constexpr int kStreamMaxRanges = 32;
@@ -729,22 +730,24 @@ __global__ void __launch_bounds__(kThreads) bt_unpack(const unsigned long long* 
   }
 }
 
-// ----------------------------------------------------- row-order int16 ---
+// ------------------------------------------------------------ row order ---
 //
-// int16 rows of kStreamMinK..kStreamMaxK centers (512 bytes to 1 KB) are
-// short for row gathers, so this path reads the CM in row order instead and
-// needs no grouping.  CTA (j, r) owns the 64-column slice j and the row range
-// r, and keeps in shared memory one 32-bit key per (center, column of the
-// slice): ((t + 32768) << 16) | (d - first row of the range), so the smaller
-// key is the lexicographically smaller (t, d) inside the range.  A thread
+// Rows of kStreamMinK..kStreamMaxK centers (512 bytes to 2 KB) are short for
+// row gathers, so this path reads the CM in row order instead and needs no
+// grouping.  CTA (j, r) owns the 128-byte column slice j (64 int16 or 32 int32
+// columns) and the row range r, and keeps in shared memory one key per
+// (center, column of the slice): ((t + 32768) << 16) | (d - first row of the
+// range) in 32 bits for int16, ((t + 2^31) << 32) | (d - first row) in 64
+// bits for int32, so the smaller key is the lexicographically smaller (t, d)
+// inside the range.  A thread
 // owns 16 bytes (8 columns) of every 128th row; each is copied into the
 // thread's own shared slot by cp.async kStreamStages rows ahead (the bytes in
 // flight are bounded by shared memory, not registers), then the thread
 // compares its keys with the table and lowers an entry with a shared atomicMin only where its
 // key is smaller (entries only decrease, so a stale read never hides a
-// smaller key).  A table row is laid out as two halves: the first 4 columns
-// of every thread's 8 at words 4 * cg, the other 4 at 32 + 4 * cg, so each
-// 128-bit shared load of 8 threads covers 32 distinct banks.  bt_own gathers
+// smaller key).  A table row (256 bytes) is laid out as two halves: the
+// first half of every thread's keys in the first 128 bytes, the other half in
+// the second, so each 128-bit shared load of 8 threads covers 32 banks.  bt_own gathers
 // CM(d, assign[d]) first; bt_merge_ranges takes, for every (u, v), the
 // smallest t over the ranges in range order (ranges ascend in d, so the first
 // range that attains it holds the smallest d) and writes tc/td.
@@ -759,25 +762,47 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Dynamic shared memory of bt_scan_stream16: the key table, then the stages.
+// Per cost type: columns per slice (128 bytes of a row), the key, and the
+// key's split into cost and row offset.  A key row is 256 bytes either way.
+template <typename T> struct StreamKey;
+template <> struct StreamKey<int16_t> {
+  using K = uint32_t;                    // ((t + 32768) << 16) | row offset
+  static constexpr int kCols = 64;
+  static __device__ __forceinline__ int32_t cost(K key) { return (int32_t)(key >> 16) - 32768; }
+  static __device__ __forceinline__ uint32_t offset(K key) { return key & 0xffffu; }
+};
+template <> struct StreamKey<int32_t> {
+  using K = unsigned long long;          // ((t + 2^31) << 32) | row offset
+  static constexpr int kCols = 32;
+  static __device__ __forceinline__ int32_t cost(K key) {
+    return (int32_t)((int64_t)(key >> 32) - 2147483648LL);
+  }
+  static __device__ __forceinline__ uint32_t offset(K key) { return (uint32_t)key; }
+};
+
+// Dynamic shared memory of bt_scan_stream: the key table, then the stages.
 static size_t stream_smem_bytes(int32_t k) {
-  return 4 * (size_t)k * kStreamCols + (size_t)kStreamStages * kStreamThreads * 16;
+  return 256 * (size_t)k + (size_t)kStreamStages * kStreamThreads * 16;
 }
 
 // Row ranges of the row-order path on `num_sms` SMs, 0 if it does not apply.
-static int stream_ranges(int32_t n, int32_t k, int num_sms) {
+// int16 keys hold a 16-bit row offset (ranges of at most kStreamRowSpan
+// rows); int32 keys are twice as wide, so at most half as many ranges fit the
+// partial tables' bytes.
+static int stream_ranges(int32_t n, int32_t k, int elem, int num_sms) {
   if (k < kStreamMinK || k > kStreamMaxK) return 0;
-  const int64_t need = ((int64_t)n + kStreamRowSpan - 1) / kStreamRowSpan;
-  if (need > kStreamMaxRanges) return 0;
-  const int nslice = (k + kStreamCols - 1) / kStreamCols;
-  int64_t r = std::max<int64_t>(need, num_sms / nslice);
-  r = std::min<int64_t>(r, kStreamMaxRanges);
-  r = std::min<int64_t>(r, n);
-  return (int)r;
+  const int cols = elem == 2 ? StreamKey<int16_t>::kCols : StreamKey<int32_t>::kCols;
+  const int64_t need = elem == 2 ? ((int64_t)n + kStreamRowSpan - 1) / kStreamRowSpan : 1;
+  const int64_t cap = elem == 2 ? std::min<int64_t>(kStreamMaxRanges, n)
+                                : std::min<int64_t>(kStreamMaxRanges / 2, n / 2);
+  if (cap < 1 || need > cap) return 0;
+  const int nslice = (k + cols - 1) / cols;
+  return (int)std::min<int64_t>(cap, std::max<int64_t>(need, num_sms / nslice));
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kThreads) bt_own(const int32_t* __restrict__ assign, int32_t n,
-                                                   int32_t k, const int16_t* __restrict__ cm,
+                                                   int32_t k, const T* __restrict__ cm,
                                                    int64_t ld, int32_t* own) {
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kThreads) {
@@ -786,29 +811,35 @@ __global__ void __launch_bounds__(kThreads) bt_own(const int32_t* __restrict__ a
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kStreamThreads, 1)
-bt_scan_stream16(const int16_t* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
-                 const int32_t* __restrict__ assign, const int32_t* __restrict__ own, int nslice,
-                 int nranges, uint32_t* part) {
+bt_scan_stream(const T* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
+               const int32_t* __restrict__ assign, const int32_t* __restrict__ own, int nslice,
+               int nranges, typename StreamKey<T>::K* part) {
+  using K = typename StreamKey<T>::K;
+  constexpr int COLS = StreamKey<T>::kCols;
+  constexpr int VPL = 16 / (int)sizeof(T);   // columns per thread (16 bytes)
+  constexpr int HALF = VPL / 2;              // keys per 16-byte half
   constexpr int P = kStreamStages;
-  extern __shared__ __align__(16) uint32_t acc[];   // k rows of kStreamCols keys, then the stages
+  extern __shared__ __align__(16) unsigned char stream_smem[];
+  K* acc = reinterpret_cast<K*>(stream_smem);   // k rows of COLS keys, then the stages
   const int tid = threadIdx.x, cg = tid & 7, rl = tid >> 3;
   const int j = blockIdx.x % nslice, r = blockIdx.x / nslice;
   const int64_t R0 = (int64_t)r * n / nranges, R1 = (int64_t)(r + 1) * n / nranges;
-  const int c0 = j * kStreamCols;
-  const int w = min(kStreamCols, k - c0);
-  const bool act = cg * 8 < w;
+  const int c0 = j * COLS;
+  const int w = min(COLS, k - c0);
+  const bool act = cg * VPL < w;
   const uint4 none = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-  for (int i = tid; i < k * kStreamCols / 4; i += kStreamThreads) reinterpret_cast<uint4*>(acc)[i] = none;
+  for (int i = tid; i < k * 16; i += kStreamThreads) reinterpret_cast<uint4*>(acc)[i] = none;
   __syncthreads();
-  const int16_t* colp = cm + c0 + cg * 8;
+  const T* colp = cm + c0 + cg * VPL;
   // rows of this thread: R0 + rl + 128 i, i < M; row i's 16 bytes go to
   // stage i % P of the thread's own shared slots P rows ahead (cp.async: a
   // thread waits only for its own copies, no barrier), its center and own
   // cost to a register ring P rows ahead
   const int64_t span = R1 - R0;
   const int32_t M = act && rl < span ? (int32_t)((span - rl + 127) / 128) : 0;
-  uint4* stage = reinterpret_cast<uint4*>(acc + k * kStreamCols);   // [P][kStreamThreads]
+  uint4* stage = reinterpret_cast<uint4*>(stream_smem + 256 * (size_t)k);   // [P][kStreamThreads]
   int32_t ra[P], ro[P];
 #pragma unroll
   for (int q = 0; q < P; ++q) {
@@ -830,24 +861,35 @@ bt_scan_stream16(const int16_t* __restrict__ cm, int64_t ld, int32_t n, int32_t 
       const int32_t i = m + q;
       if (i < M && a >= 0 && a < k) {
         const uint4 x = stage[q * kStreamThreads + tid];
-        const uint32_t crow = ((uint32_t)(32768 - o) << 16) | (uint32_t)(rl + 128 * i);
-        uint32_t* row = acc + a * kStreamCols;
-        uint32_t* lo_p = row + 4 * cg;
-        uint32_t* hi_p = row + 32 + 4 * cg;
+        const uint32_t off = (uint32_t)(rl + 128 * i);
+        // the thread's first HALF keys sit in the row's first 128 bytes, the
+        // others in the second: 8 threads' 16-byte loads cover 32 banks
+        K* lo_p = acc + a * COLS + HALF * cg;
+        K* hi_p = lo_p + COLS / 2;
+        K key[VPL];
+        if constexpr (sizeof(T) == 2) {
+          const uint32_t crow = ((uint32_t)(32768 - o) << 16) | off;
+          const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            key[2 * h] = (w4[h] << 16) + crow;
+            key[2 * h + 1] = (w4[h] & 0xffff0000u) + crow;
+          }
+        } else {
+          const int32_t w4[4] = {(int32_t)x.x, (int32_t)x.y, (int32_t)x.z, (int32_t)x.w};
+#pragma unroll
+          for (int h = 0; h < 4; ++h)
+            key[h] = ((K)(uint32_t)((int64_t)w4[h] - o + 2147483648LL) << 32) | off;
+        }
         const uint4 lo = *reinterpret_cast<const uint4*>(lo_p);
         const uint4 hi = *reinterpret_cast<const uint4*>(hi_p);
-        const uint32_t k0 = (x.x << 16) + crow, k1 = (x.x & 0xffff0000u) + crow;
-        const uint32_t k2 = (x.y << 16) + crow, k3 = (x.y & 0xffff0000u) + crow;
-        const uint32_t k4 = (x.z << 16) + crow, k5 = (x.z & 0xffff0000u) + crow;
-        const uint32_t k6 = (x.w << 16) + crow, k7 = (x.w & 0xffff0000u) + crow;
-        if (k0 < lo.x) atomicMin(lo_p + 0, k0);
-        if (k1 < lo.y) atomicMin(lo_p + 1, k1);
-        if (k2 < lo.z) atomicMin(lo_p + 2, k2);
-        if (k3 < lo.w) atomicMin(lo_p + 3, k3);
-        if (k4 < hi.x) atomicMin(hi_p + 0, k4);
-        if (k5 < hi.y) atomicMin(hi_p + 1, k5);
-        if (k6 < hi.z) atomicMin(hi_p + 2, k6);
-        if (k7 < hi.w) atomicMin(hi_p + 3, k7);
+        const K* cl = reinterpret_cast<const K*>(&lo);
+        const K* ch = reinterpret_cast<const K*>(&hi);
+#pragma unroll
+        for (int h = 0; h < HALF; ++h) {
+          if (key[h] < cl[h]) atomicMin(lo_p + h, key[h]);
+          if (key[HALF + h] < ch[h]) atomicMin(hi_p + h, key[HALF + h]);
+        }
       }
       // stage q now takes row i + P
       const int32_t nx = i + P;
@@ -863,35 +905,64 @@ bt_scan_stream16(const int16_t* __restrict__ cm, int64_t ld, int32_t n, int32_t 
   }
   cp_async_wait<0>();
   __syncthreads();
-  uint32_t* out = part + (int64_t)r * k * k;
-  for (int i = tid; i < k * kStreamCols; i += kStreamThreads) {
-    const int u = i / kStreamCols, pc = i % kStreamCols;
-    const int col = pc < 32 ? 8 * (pc >> 2) + (pc & 3) : 8 * ((pc - 32) >> 2) + 4 + (pc & 3);
+  K* out = part + (int64_t)r * k * k;
+  for (int i = tid; i < k * COLS; i += kStreamThreads) {
+    const int u = i / COLS, pc = i % COLS;   // pc: key slot in the row; its column:
+    const int hh = pc / (COLS / 2), rest = pc % (COLS / 2);
+    const int col = (rest / HALF) * VPL + hh * HALF + rest % HALF;
     if (col < w) out[(int64_t)u * k + c0 + col] = acc[i];
   }
 }
 
-__global__ void __launch_bounds__(kThreads) bt_merge_ranges(const uint32_t* __restrict__ part,
+template <typename K, typename T>
+__global__ void __launch_bounds__(kThreads) bt_merge_ranges(const K* __restrict__ part,
                                                             int nranges, int32_t n, int32_t k,
                                                             int32_t* tc, int32_t* td) {
   const int64_t kk = (int64_t)k * k;
+  const K none = ~(K)0;
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < kk;
        i += (int64_t)gridDim.x * kThreads) {
-    uint32_t best = 0xffffffffu;
+    K best = none;
     int br = -1;
     for (int r = 0; r < nranges; ++r) {
-      const uint32_t key = part[r * kk + i];
-      if (key != 0xffffffffu && (br < 0 || (key >> 16) < (best >> 16))) { best = key; br = r; }
+      const K key = part[r * kk + i];
+      if (key != none &&
+          (br < 0 || StreamKey<T>::cost(key) < StreamKey<T>::cost(best))) { best = key; br = r; }
     }
     const int32_t u = (int32_t)(i / k), v = (int32_t)(i % k);
     if (br < 0 || u == v) {
       tc[i] = kTInf;
       td[i] = -1;
     } else {
-      tc[i] = (int32_t)(best >> 16) - 32768;
-      td[i] = (int32_t)((int64_t)br * n / nranges + (best & 0xffffu));
+      tc[i] = StreamKey<T>::cost(best);
+      td[i] = (int32_t)((int64_t)br * n / nranges + StreamKey<T>::offset(best));
     }
   }
+}
+
+template <typename T>
+static cudaError_t stream_run(const T* cm, int64_t ld, int32_t n, int32_t k, const int32_t* assign,
+                              int32_t* tc, int32_t* td, const BtWorkspace& W, int nranges,
+                              cudaStream_t st, int num_sms) {
+  using K = typename StreamKey<T>::K;
+  static std::atomic<uint64_t> attr_set{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!(attr_set.load() & (1ull << dev))) {
+    e = cudaFuncSetAttribute(bt_scan_stream<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)stream_smem_bytes(kStreamMaxK));
+    if (e != cudaSuccess) return e;
+    attr_set.fetch_or(1ull << dev);
+  }
+  const int nslice = (k + StreamKey<T>::kCols - 1) / StreamKey<T>::kCols;
+  K* part = reinterpret_cast<K*>(W.part);
+  bt_own<T><<<num_sms * 4, kThreads, 0, st>>>(assign, n, k, cm, ld, W.perm);
+  bt_scan_stream<T><<<nslice * nranges, kStreamThreads, stream_smem_bytes(k), st>>>(
+      cm, ld, n, k, assign, W.perm, nslice, nranges, part);
+  bt_merge_ranges<K, T><<<num_sms * 4, kThreads, 0, st>>>(part, nranges, n, k, tc, td);
+  return cudaGetLastError();
 }
 
 int bt_max_k(int elem_bytes) { return kThreads * (16 / elem_bytes); }
@@ -935,27 +1006,13 @@ cudaError_t best_transfer_run(int32_t n, int32_t k, const void* cm, int elem_byt
                               cudaStream_t st, int num_sms) {
   void* base = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
   const BtWorkspace W = carve(base, n, k);
-  const int nranges = elem_bytes == 2 ? stream_ranges(n, k, num_sms) : 0;
-  if (nranges > 0) {
-    static std::atomic<uint64_t> attr_set{0};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!(attr_set.load() & (1ull << dev))) {
-      e = cudaFuncSetAttribute(bt_scan_stream16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)stream_smem_bytes(kStreamMaxK));
-      if (e != cudaSuccess) return e;
-      attr_set.fetch_or(1ull << dev);
-    }
-    const int16_t* cm16 = static_cast<const int16_t*>(cm);
-    const int nslice = (k + kStreamCols - 1) / kStreamCols;
-    bt_own<<<num_sms * 4, kThreads, 0, st>>>(assign, n, k, cm16, ld, W.perm);
-    bt_scan_stream16<<<nslice * nranges, kStreamThreads, stream_smem_bytes(k), st>>>(
-        cm16, ld, n, k, assign, W.perm, nslice, nranges, W.part);
-    bt_merge_ranges<<<num_sms * 4, kThreads, 0, st>>>(W.part, nranges, n, k, tc, td);
-    return cudaGetLastError();
-  }
+  const int nranges = stream_ranges(n, k, elem_bytes, num_sms);
+  if (nranges > 0)
+    return elem_bytes == 2
+               ? stream_run(static_cast<const int16_t*>(cm), ld, n, k, assign, tc, td, W, nranges,
+                            st, num_sms)
+               : stream_run(static_cast<const int32_t*>(cm), ld, n, k, assign, tc, td, W, nranges,
+                            st, num_sms);
   cudaError_t e = cudaMemsetAsync(W.ctl, 0, 4 * BT_CTL_WORDS + 4ull * (k + 1), st);
   if (e != cudaSuccess) return e;
   bt_count<<<kTiles, kTileThreads, 4 * (size_t)k, st>>>(assign, n, k, W.cnt, W.tile_rel);

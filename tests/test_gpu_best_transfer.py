@@ -151,8 +151,8 @@ def test_large_snapshot_full_size(gpu_lib):
 
 
 # Row widths on both sides of the 512-byte switch between the register scan
-# and the bulk-copy scan, both ends of the int16 row-order path (256 to 512
-# centers, several row ranges), the largest k of each storage type, and allotments
+# and the bulk-copy scan, both ends of the row-order path (256 to 512 centers,
+# int16 and int32, several row ranges), the largest k of each storage type, and allotments
 # with many equal costs (scale 3: CM in 1..6) where one center holds most
 # units, so that its rows are split over many work items and equal-cost
 # candidates from different items meet in the table merge.
@@ -170,6 +170,9 @@ SHAPE_CASES = [  # (n, k, dtype, scale, skew)
     (140000, 512, "i16", 3.0, True),      # row-order path: three row ranges at least, ties
     (3, 300, "i16", 100.0, False),        # row-order path with one row per range
     (70000, 513, "i16", 100.0, True),     # just past the row-order path: row gathers
+    (140000, 512, "i32", 3.0, True),      # int32 row-order path (64-bit keys), ties
+    (3, 300, "i32", 100.0, False),        # int32 row-order path, one range
+    (1, 300, "i32", 100.0, False),        # one unit: no int32 range fits, row gathers
 ]
 
 
