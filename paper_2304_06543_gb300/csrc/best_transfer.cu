@@ -69,7 +69,6 @@ struct BtWorkspace {
 // int32: at most kStreamMaxRanges / 2 ranges (twice as wide keys, the same
 // bytes of partial tables).
 constexpr int kStreamMinK = 256, kStreamMaxK = 512;
-constexpr int kStreamCols = 64;          // columns per slice: 128 bytes of a row
 constexpr int kStreamMaxRanges = 32;
 constexpr int64_t kStreamRowSpan = 65536;  // the 16-bit row offset of a key
 
@@ -780,6 +779,13 @@ template <> struct StreamKey<int32_t> {
   static __device__ __forceinline__ uint32_t offset(K key) { return (uint32_t)key; }
 };
 
+// Programmatic dependent launch: a kernel launched with the attribute may
+// start while its predecessor on the stream still runs; it waits here until
+// the predecessor's results are visible (a no-op for an ordinary launch).
+__device__ __forceinline__ void wait_predecessor() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next kernel on the stream start launching.
+__device__ __forceinline__ void release_successor() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Dynamic shared memory of bt_scan_stream: the key table, then the stages.
 static size_t stream_smem_bytes(int32_t k) {
   return 256 * (size_t)k + (size_t)kStreamStages * kStreamThreads * 16;
@@ -804,6 +810,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) bt_own(const int32_t* __restrict__ assign, int32_t n,
                                                    int32_t k, const T* __restrict__ cm,
                                                    int64_t ld, int32_t* own) {
+  release_successor();
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kThreads) {
     const int32_t a = assign[i];
@@ -832,6 +839,7 @@ bt_scan_stream(const T* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
   const uint4 none = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
   for (int i = tid; i < k * 16; i += kStreamThreads) reinterpret_cast<uint4*>(acc)[i] = none;
   __syncthreads();
+  wait_predecessor();   // own[] comes from bt_own
   const T* colp = cm + c0 + cg * VPL;
   // rows of this thread: R0 + rl + 128 i, i < M; row i's 16 bytes go to
   // stage i % P of the thread's own shared slots P rows ahead (cp.async: a
@@ -904,6 +912,7 @@ bt_scan_stream(const T* __restrict__ cm, int64_t ld, int32_t n, int32_t k,
     }
   }
   cp_async_wait<0>();
+  release_successor();
   __syncthreads();
   K* out = part + (int64_t)r * k * k;
   for (int i = tid; i < k * COLS; i += kStreamThreads) {
@@ -918,6 +927,7 @@ template <typename K, typename T>
 __global__ void __launch_bounds__(kThreads) bt_merge_ranges(const K* __restrict__ part,
                                                             int nranges, int32_t n, int32_t k,
                                                             int32_t* tc, int32_t* td) {
+  wait_predecessor();   // the partial tables come from bt_scan_stream
   const int64_t kk = (int64_t)k * k;
   const K none = ~(K)0;
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < kk;
@@ -959,9 +969,26 @@ static cudaError_t stream_run(const T* cm, int64_t ld, int32_t n, int32_t k, con
   const int nslice = (k + StreamKey<T>::kCols - 1) / StreamKey<T>::kCols;
   K* part = reinterpret_cast<K*>(W.part);
   bt_own<T><<<num_sms * 4, kThreads, 0, st>>>(assign, n, k, cm, ld, W.perm);
-  bt_scan_stream<T><<<nslice * nranges, kStreamThreads, stream_smem_bytes(k), st>>>(
-      cm, ld, n, k, assign, W.perm, nslice, nranges, part);
-  bt_merge_ranges<K, T><<<num_sms * 4, kThreads, 0, st>>>(part, nranges, n, k, tc, td);
+  // the next two kernels may launch before their predecessor ends; each waits
+  // for it (wait_predecessor) before reading its results
+  cudaLaunchAttribute pdl[1];
+  pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  pdl[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.stream = st;
+  cfg.attrs = pdl;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(nslice * nranges);
+  cfg.blockDim = dim3(kStreamThreads);
+  cfg.dynamicSmemBytes = stream_smem_bytes(k);
+  e = cudaLaunchKernelEx(&cfg, bt_scan_stream<T>, cm, ld, n, k, assign, (const int32_t*)W.perm,
+                         nslice, nranges, part);
+  if (e != cudaSuccess) return e;
+  cfg.gridDim = dim3(num_sms * 4);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 0;
+  e = cudaLaunchKernelEx(&cfg, bt_merge_ranges<K, T>, (const K*)part, nranges, n, k, tc, td);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
