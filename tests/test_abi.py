@@ -54,6 +54,21 @@ def test_host_side_calls(lib):
     lib.lbdd_destroy(None)
 
 
+@pytest.mark.parametrize("n,k", [(1, 300), (3, 256), (20, 500), (200000, 500), (140000, 512),
+                                 (2000000, 2000), (9000, 4096), (50, 7)])
+def test_best_transfer_workspace_covers_every_path(lib, n, k):
+    """The scan's workspace holds, at least, the allotted units grouped by
+    center (4n), the packed k x k table (8k^2), the work items (16 (n/64 + k)),
+    and for 256..512 centers the row-order path's per-range key tables: 32-bit
+    keys in up to 32 ranges (int16) or 64-bit keys in up to 16 (int32), both
+    4k^2 x min(32, n) bytes."""
+    import paper_2304_06543_gb300 as lb
+    need = 4 * n + 8 * k * k + 16 * (n // 64 + k)
+    if 256 <= k <= 512:
+        need += 4 * k * k * min(32, n)
+    assert lb.best_transfer_workspace(n, k) >= need
+
+
 def test_product_does_not_reference_oracle():
     """The CUDA path and its binding never import or link the oracle."""
     pkg = os.path.join(ROOT, "paper_2304_06543_gb300")
